@@ -1,0 +1,195 @@
+"""Plain FP64 CPU oracle of the direct-summation gravity pass.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may use it.  The
+GPU library never imports, links or calls anything here, and nothing here
+imports the GPU library.
+
+Contents
+--------
+``predict``           Taylor predictor of the sources (Sec. 2.2), sp2_oracle.c
+``forces``            direct sum of acc / jerk / snap / pot / nearest neighbour
+                      with per-sink scale sums (Sec. 3), sp2_oracle.c
+``step``              predict + forces on sink slots, the block-step pass
+``energy``            kinetic + potential energy
+``hermite4_shared``   shared-step 4th-order Hermite integrator (test driver)
+``adjoint``           float64 torch restatement for gradient checks (adjoint.py)
+
+Parity status: every output is pinned by the ``-m "not gpu"`` tests
+(brute force in 50-digit decimal arithmetic, two-body Kepler closed form,
+Newton's third law, pair-sum symmetry, finite differences along the predictor,
+invariances, Hermite energy conservation).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "sp2_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB_PATH = _BUILD / "libsp2_oracle.so"
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile sp2_oracle.c into oracle/_build/libsp2_oracle.so (gcc, OpenMP)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp.so")
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-std=c11", str(_SRC), "-o", str(tmp), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(str(_LIB_PATH))
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        lib.sp2o_predict.argtypes = [I64, ctypes.c_int, ctypes.c_double, P, P, P, P, P, P, P, P, P]
+        lib.sp2o_predict.restype = None
+        lib.sp2o_forces.argtypes = [I64, P, P, P, P, I64, P, P, P, P, P,
+                                    ctypes.c_double, ctypes.c_int,
+                                    P, P, P, P, P, P, P, P, P]
+        lib.sp2o_forces.restype = None
+        lib.sp2o_max_threads.restype = ctypes.c_int
+        lib.sp2o_set_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().sp2o_max_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().sp2o_set_threads(int(n))
+
+
+def predict(t, tj, x, v, a, jerk, snap=None, order: int = 4):
+    """Taylor-predict sources to time t; returns (xp, vp, ap) (ap None for order 4)."""
+    lib = _load()
+    n = len(tj)
+    tj = _f64(tj, (n,))
+    x, v, a, jerk = (_f64(q, (n, 3)) for q in (x, v, a, jerk))
+    xp = np.empty((n, 3))
+    vp = np.empty((n, 3))
+    ap = None
+    sn = None
+    if order == 6:
+        if snap is None:
+            raise ValueError("order 6 needs snap")
+        sn = _f64(snap, (n, 3))
+        ap = np.empty((n, 3))
+    lib.sp2o_predict(n, order, float(t), _p(tj), _p(x), _p(v), _p(a), _p(jerk), _p(sn),
+                     _p(xp), _p(vp), _p(ap))
+    return xp, vp, ap
+
+
+def forces(ids_i, xi, vi, ids_j, mj, xj, vj, eps2: float, order: int = 4, ai=None, aj=None):
+    """Direct sum on explicit sinks.  Returns a dict of numpy arrays.
+
+    Keys: acc, jerk, snap (order 6), pot, nn_id, nn_r2, sc_acc, sc_jerk, sc_snap.
+    """
+    lib = _load()
+    n_i, n_j = len(ids_i), len(ids_j)
+    ids_i = np.ascontiguousarray(ids_i, dtype=np.int32)
+    ids_j = np.ascontiguousarray(ids_j, dtype=np.int32)
+    xi, vi = _f64(xi, (n_i, 3)), _f64(vi, (n_i, 3))
+    xj, vj = _f64(xj, (n_j, 3)), _f64(vj, (n_j, 3))
+    mj = _f64(mj, (n_j,))
+    if order == 6:
+        if ai is None or aj is None:
+            raise ValueError("order 6 needs ai and aj")
+        ai, aj = _f64(ai, (n_i, 3)), _f64(aj, (n_j, 3))
+    else:
+        ai = aj = None
+    out = {
+        "acc": np.empty((n_i, 3)), "jerk": np.empty((n_i, 3)),
+        "snap": np.empty((n_i, 3)) if order == 6 else None,
+        "pot": np.empty(n_i), "nn_id": np.empty(n_i, dtype=np.int32), "nn_r2": np.empty(n_i),
+        "sc_acc": np.empty(n_i), "sc_jerk": np.empty(n_i),
+        "sc_snap": np.empty(n_i) if order == 6 else None,
+    }
+    lib.sp2o_forces(n_i, _p(ids_i), _p(xi), _p(vi), _p(ai),
+                    n_j, _p(ids_j), _p(mj), _p(xj), _p(vj), _p(aj),
+                    float(eps2), int(order),
+                    _p(out["acc"]), _p(out["jerk"]), _p(out["snap"]), _p(out["pot"]),
+                    _p(out["nn_id"]), _p(out["nn_r2"]),
+                    _p(out["sc_acc"]), _p(out["sc_jerk"]), _p(out["sc_snap"]))
+    if order != 6:
+        del out["snap"], out["sc_snap"]
+    return out
+
+
+def step(t, i_idx, ids, m, tj, x, v, a, jerk, snap=None, *, eps2: float, order: int = 4,
+         j_range=None):
+    """One block-step force pass: predict every source to t, then sum on sinks.
+
+    The sinks are the predicted sources at slots ``i_idx`` (the i-particles are
+    j-particles due for an update).  ``j_range=(lo, hi)`` restricts the sources
+    to slots lo..hi-1 (one independent system of a batch).
+    """
+    xp, vp, ap = predict(t, tj, x, v, a, jerk, snap, order)
+    i_idx = np.asarray(i_idx, dtype=np.int64)
+    lo, hi = (0, len(ids)) if j_range is None else j_range
+    sl = slice(lo, hi)
+    return forces(ids[i_idx], xp[i_idx], vp[i_idx], ids[sl], m[sl], xp[sl], vp[sl],
+                  eps2, order,
+                  ai=None if ap is None else ap[i_idx], aj=None if ap is None else ap[sl])
+
+
+def energy(m, x, v, eps2: float) -> float:
+    """Total energy: sum m v^2 / 2 + (1/2) sum m_i pot_i, with the oracle's pot."""
+    n = len(m)
+    ids = np.arange(n, dtype=np.int32)
+    f = forces(ids, x, v, ids, m, x, v, eps2, 4)
+    return float(0.5 * np.sum(m * np.sum(v * v, axis=1)) + 0.5 * np.sum(m * f["pot"]))
+
+
+def hermite4_shared(m, x, v, eps2: float, dt: float, n_steps: int):
+    """Shared-time-step 4th-order Hermite integration (Makino & Aarseth 1992).
+
+    Per step: predict with the Taylor polynomial, evaluate acc and jerk at the
+    predicted state, then correct
+        v1 = v0 + (a0 + a1) dt/2 + (j0 - j1) dt^2/12
+        x1 = x0 + (v0 + v1) dt/2 + (a0 - a1) dt^2/12.
+    Returns the final (x, v).  The integrator around the force pass is driver
+    code of the tests; the paper leaves it to the user (Sec. 3.7).
+    """
+    n = len(m)
+    ids = np.arange(n, dtype=np.int32)
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    f = forces(ids, x, v, ids, m, x, v, eps2, 4)
+    a0, j0 = f["acc"], f["jerk"]
+    tj = np.zeros(n)
+    for _ in range(n_steps):
+        xp, vp, _ = predict(dt, tj, x, v, a0, j0, None, 4)
+        f = forces(ids, xp, vp, ids, m, xp, vp, eps2, 4)
+        a1, j1 = f["acc"], f["jerk"]
+        v1 = v + (a0 + a1) * (dt / 2) + (j0 - j1) * (dt * dt / 12)
+        x1 = x + (v + v1) * (dt / 2) + (a0 - a1) * (dt * dt / 12)
+        x, v, a0, j0 = x1, v1, a1, j1
+    return x, v
