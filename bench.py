@@ -1,0 +1,485 @@
+"""Benchmark of the direct-summation gravity pass on GB300.
+
+Headline workload: block time-step Hermite-4 in mixed precision, N = 131072
+equal-mass Plummer sphere, eps = 1e-4, N_active = 131072 (all sinks), with
+nearest neighbours.  One step = the whole hot path: copy kernel for the
+N_active updated particles, predictor for all N sources, force pass (and the
+split-j reduction when the launch shape uses one).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is interactions/s (N_active x N per step,
+self pair counted) over all ranks with inputs resident in HBM; `e2e` is the
+same metric through the C ABI with pinned host buffers (host->device copy of
+the updated particles and sink list, device->host copy of every output,
+inside the timed region).  With --gpus N > 1 (torchrun) every rank runs an
+independent replica (weak scaling); there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "interactions/s & %FP32 peak vs N_active; mixed/batched/adjoint vs FP64"
+UNIT = "interactions/s"
+WORKLOAD = "Plummer N=131072, eps=1e-4, Hermite-4 block step, mixed precision (double-single positions, FP32 terms, FP64 reduction), N_active=131072, with nearest neighbour"
+# FP32-pipe instructions per interaction of the mixed Hermite-4 pass with
+# nearest neighbour (the algorithmic count): 9 double-single
+# difference, 3 dv, 3 r^2, 1 softening add, 4 (rinv^2, m rinv, m rinv^3, pot),
+# 3 r.v, 2 alpha, 3 acc, 6 jerk, 2 nearest-neighbour compare/select.
+OPS_PER_INTERACTION = 36
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=131072)
+    p.add_argument("--n-active", type=int, default=131072)
+    p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint lines")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [q.strip() for q in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def make_workload(n, n_active, seed=0):
+    m, x, v = W.plummer(n, seed)
+    a, jk, _ = W.derivative_noise(n, seed + 1, scales=(1.0, 4.0, 16.0))
+    ids = W.particle_ids(n)
+    t = 1.0
+    tj = W.block_times(n, seed + 2, t)
+    idx = W.active_set(n, n_active, seed + 1000)
+    return dict(m=m, x=x, v=v, a=a, jerk=jk, ids=ids, tj=tj, t=t, idx=idx)
+
+
+def run_reference(args, world, rank):
+    """The oracle, as it stands, on the host cores (the slow reference arm)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = make_workload(args.n, args.n_active)
+    sample = int(min(args.n_active, 512))
+    idx = w["idx"][:sample]
+    step = lambda: oracle.step(w["t"], idx, w["ids"], w["m"], w["tj"], w["x"], w["v"], w["a"],  # noqa: E731
+                               w["jerk"], None, eps2=1e-8, order=4)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    inter = args.steps * sample * args.n
+    val = inter / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_sinks_per_step": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{sample} of the {args.n_active} sinks per step against all {args.n} "
+                                       f"sources, predictor over all {args.n}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, n, budget_s=12.0):
+    import oracle
+    oracle.build()
+    step = lambda k: oracle.step(w["t"], w["idx"][:k], w["ids"], w["m"], w["tj"], w["x"], w["v"], w["a"],  # noqa: E731
+                                 w["jerk"], None, eps2=1e-8, order=4)
+    k0 = min(256, len(w["idx"]))
+    t0 = time.perf_counter()
+    step(k0)
+    rate = k0 * n / max(time.perf_counter() - t0, 1e-6)
+    k = int(min(len(w["idx"]), max(k0, budget_s * rate / n)))
+    t0 = time.perf_counter()
+    step(k)
+    dt = time.perf_counter() - t0
+    return {"value": k * n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{k} of the {len(w['idx'])} active sinks against all {n} sources "
+                      f"(plus the predictor over all {n}), {dt:.1f} s"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1510_04068_gb300 import build as libbuild
+    from paper_1510_04068_gb300 import sp2
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (the library has no CPU path)"
+    torch.cuda.set_device(local)
+    libbuild.build()
+    sp2.load()
+    dev = torch.device("cuda", local)
+    n, n_act = args.n, args.n_active
+    w = make_workload(n, n_act, seed=rank)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    idx_h = w["idx"]
+    stream = torch.cuda.Stream(device=dev)
+    eps2 = 1e-8
+    full = {k: D(w[k]) for k in ("ids", "m", "x", "v", "a", "jerk", "tj")}
+    upd = {k: full[k][torch.as_tensor(idx_h.astype(np.int64), device=dev)].contiguous() for k in full}
+    idx = D(idx_h)
+    out = dict(acc=torch.empty((n_act, 3), dtype=torch.float64, device=dev),
+               jerk=torch.empty((n_act, 3), dtype=torch.float64, device=dev),
+               pot=torch.empty(n_act, dtype=torch.float64, device=dev),
+               nn_id=torch.empty(n_act, dtype=torch.int32, device=dev),
+               nn_r2=torch.empty(n_act, dtype=torch.float64, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        ctx = sp2.Context(order=4, precision=sp2.SP2_MIXED, n_max=n, eps2=eps2, profile=1,
+                          cuda_stream=stream.cuda_stream)
+        ctx.set_j(0, full["ids"], full["m"], full["x"], full["v"], full["a"], full["jerk"], None, full["tj"])
+        ctx.predict(w["t"])
+        tuned = None if args.no_tune else ctx.autotune(n_act)
+        launch = ctx.get_launch(n_act)
+
+        def step(k):
+            ctx.set_j(0, upd["ids"], upd["m"], upd["x"], upd["v"], upd["a"], upd["jerk"], None, upd["tj"],
+                      slots=idx)
+            ctx.predict(w["t"] + k * 2.0 ** -20)
+            ctx.compute(idx, **out)
+
+        for k in range(args.warmup):
+            step(k)
+            flush.zero_()
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        ctx.profile_reset()
+        l0 = ctx.kernel_launches()
+        with ClockSampler(local) as clk:
+            wall0 = time.perf_counter()
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                step(k)
+                ev[k][1].record(stream)
+                flush.zero_()
+            stream.synchronize()
+            wall1 = time.perf_counter()
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = ctx.kernel_launches() - l0
+        prof = ctx.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = allmax(world, sum(step_ms))
+    inter_step = n_act * n
+    value = world * args.steps * inter_step / (total_ms / 1e3)
+    fcount, fms = prof["force"]
+    force_ms = fms / max(fcount, 1)
+    dev_props = torch.cuda.get_device_properties(dev)
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    peak_tops = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    achieved = inter_step * OPS_PER_INTERACTION / (force_ms / 1e3) / 1e12
+    clocks = clk.summary()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "n_active": n_act, "order": 4, "precision": "mixed",
+                   "eps": 1e-4, "nearest_neighbour": True, "parallelism": f"replicas{world}",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, outside the step events)",
+                   "launch": launch, "autotuned": tuned is not None,
+                   "wall_ms_incl_flush": 1e3 * (wall1 - wall0) / args.steps},
+        "stages_ms_per_step": {k: (v[1] / args.steps) for k, v in prof.items() if v[0]},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (FP32 lane-instr)",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "kernel": "pass_kernel<MixedForce<4,NN>>", "force_ms_per_launch": force_ms,
+                     "ops_per_interaction": OPS_PER_INTERACTION,
+                     "peak_basis": f"{dev_props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                                   f"(max SM clock, MEASURED_PEAKS.json)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, n)
+    if not args.no_e2e:
+        line["e2e"] = e2e(ctx, w, upd, out, args, stream)
+    if not args.no_extras and rank == 0:
+        line["detail"] = extras(sp2, w, n, eps2, dev, stream)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e(ctx, w, upd, out, args, stream):
+    """Same step through the C ABI with pinned host buffers; copies in the timed region."""
+    import torch
+    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+    hu = {k: pin(v) for k, v in upd.items()}
+    hidx = pin(torch.as_tensor(w["idx"]))
+    ho = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    n_act = len(w["idx"])
+
+    def step(k):
+        ctx.set_j(0, hu["ids"], hu["m"], hu["x"], hu["v"], hu["a"], hu["jerk"], None, hu["tj"], slots=hidx)
+        ctx.predict(w["t"] + k * 2.0 ** -20)
+        ctx.compute(hidx, **ho)
+
+    with torch.cuda.stream(stream):
+        for k in range(max(1, args.warmup)):
+            step(k)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step(k)
+        dt = time.perf_counter() - t0
+    h2d = sum(v.numel() * v.element_size() for v in hu.values()) + 2 * hidx.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in ho.values())
+    return {"value": args.steps * n_act * len(w["m"]) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * dt / args.steps}
+
+
+def timed(fn, reps, stream):
+    import torch
+    fn()
+    stream.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        stream.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def extras(sp2, w, n, eps2, dev, stream):
+    """N_active sweep (mixed vs FP64), batched systems, adjoint: secondary lines."""
+    import torch
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    res = {"sweep": []}
+    full = {k: D(w[k]) for k in ("ids", "m", "x", "v", "a", "jerk", "tj")}
+    with torch.cuda.stream(stream):
+        ctxs = {}
+        for prec in (sp2.SP2_MIXED, sp2.SP2_FP64):
+            c = sp2.Context(order=4, precision=prec, n_max=n, eps2=eps2, cuda_stream=stream.cuda_stream)
+            c.set_j(0, full["ids"], full["m"], full["x"], full["v"], full["a"], full["jerk"], None, full["tj"])
+            c.predict(w["t"])
+            ctxs[prec] = c
+        for na in (1, 8, 64, 1024, 16384, 131072):
+            idx = D(W.active_set(n, na, 1000 + na))
+            o = dict(acc=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                     jerk=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                     pot=torch.empty(na, dtype=torch.float64, device=dev),
+                     nn_id=torch.empty(na, dtype=torch.int32, device=dev),
+                     nn_r2=torch.empty(na, dtype=torch.float64, device=dev))
+            row = {"n_active": na}
+            for prec, name in ((sp2.SP2_MIXED, "mixed"), (sp2.SP2_FP64, "fp64")):
+                c = ctxs[prec]
+                if name == "fp64" and na > 16384:
+                    reps = 2
+                else:
+                    reps = 20
+                c.autotune(na) if (name == "mixed" or na <= 1024) else None
+                fn = lambda: (c.predict(w["t"]), c.compute(idx, **o))  # noqa: E731
+                ms = timed(fn, reps, stream)
+                row[f"{name}_us_per_step"] = 1e3 * ms
+                row[f"{name}_interactions_per_s"] = na * n / (ms / 1e3)
+                if name == "mixed":
+                    sp2.sp2_graph_begin(c.ctx)
+                    fn()
+                    g = sp2.sp2_graph_end(c.ctx)
+                    gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), reps, stream)
+                    sp2.sp2_graph_destroy(g)
+                    row["mixed_graph_us_per_step"] = 1e3 * gms
+            row["mixed_over_fp64"] = row["mixed_interactions_per_s"] / row["fp64_interactions_per_s"]
+            res["sweep"].append(row)
+        for c in ctxs.values():
+            c.close()
+        res["batched"] = bench_batched(sp2, dev, stream)
+        res["adjoint"] = bench_adjoint(dev, stream)
+    return res
+
+
+def bench_batched(sp2, dev, stream):
+    import torch
+    offsets, m, x, v = W.planetary_systems(4096, 7)
+    total = int(offsets[-1])
+    z = np.zeros((total, 3))
+    ids = W.particle_ids(total)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    c = sp2.Context(order=4, precision=sp2.SP2_MIXED, n_max=total, eps2=0.0, cuda_stream=stream.cuda_stream)
+    c.set_j(0, D(ids), D(m), D(x), D(v), D(z), D(z), None, D(np.zeros(total)))
+    c.predict(0.0)
+    plan = c.batch_plan(offsets)
+    o = dict(acc=torch.empty((total, 3), dtype=torch.float64, device=dev),
+             jerk=torch.empty((total, 3), dtype=torch.float64, device=dev),
+             pot=torch.empty(total, dtype=torch.float64, device=dev),
+             nn_id=torch.empty(total, dtype=torch.int32, device=dev),
+             nn_r2=torch.empty(total, dtype=torch.float64, device=dev))
+    one = lambda: c.compute_batched(plan, **o)  # noqa: E731
+    sp2.sp2_graph_begin(c.ctx)
+    c.predict(0.0)
+    one()
+    g = sp2.sp2_graph_end(c.ctx)
+    g_ms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), 20, stream)
+    k_ms = timed(one, 20, stream)
+    slots = D(np.arange(total, dtype=np.int32))
+
+    def per_system():
+        for s in range(4096):
+            a, b = int(offsets[s]), int(offsets[s + 1])
+            c.compute(slots[a:b], j_range=(a, b), acc=o["acc"][a:b], jerk=o["jerk"][a:b], pot=o["pot"][a:b],
+                      nn_id=o["nn_id"][a:b], nn_r2=o["nn_r2"][a:b])
+
+    s_ms = timed(per_system, 3, stream)
+    sp2.sp2_graph_destroy(g)
+    sp2.sp2_batch_plan_destroy(plan)
+    c.close()
+    inter = float(np.sum(np.diff(offsets) ** 2))
+    return {"systems": 4096, "bodies": total, "interactions": inter, "batched_us": 1e3 * k_ms,
+            "batched_graph_us_incl_predict": 1e3 * g_ms, "per_system_launches_us": 1e3 * s_ms,
+            "speedup_vs_per_system": s_ms / k_ms, "interactions_per_s": inter / (k_ms / 1e3)}
+
+
+def bench_adjoint(dev, stream):
+    import torch
+    from paper_1510_04068_gb300 import autograd as AG
+    n, steps, dt = 16384, 32, 1.0 / 256
+    m, x, v = W.plummer(n, 5)
+    w = np.random.default_rng(1005).standard_normal((n, 3))
+    T = lambda q: torch.as_tensor(q, device=dev)  # noqa: E731
+    x0, v0, mm = T(x).requires_grad_(True), T(v).requires_grad_(True), T(m).requires_grad_(True)
+    ww = T(w)
+    sim = AG.HermiteSim(n, eps2=1e-6, precision="mixed", stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xf, vf = sim.trajectory(x0, v0, mm, dt, steps, checkpoint_every=8)
+    loss = (ww * xf).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    sim.close()
+    inter = n * n * steps
+    return {"n": n, "steps": steps, "forward_ms": 1e3 * (t1 - t0), "backward_ms": 1e3 * (t2 - t1),
+            "forward_interactions_per_s": inter / (t1 - t0), "backward_over_forward": (t2 - t1) / (t1 - t0)}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * sapporo_gb.h -- C ABI of the GB300 (sm_103a) direct-summation gravity library.
+ *
+ * The library implements the hot path of the Sapporo2 method (Bedorf, Gaburov &
+ * Portegies Zwart 2015): store j-particles (sources) in FP64, Taylor-predict
+ * them to a common time, and sum over them, for a list of active i-particles
+ * (sinks), the Plummer-softened acceleration, jerk, snap (6th order),
+ * potential and nearest neighbour.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units: G = 1.  Potential is negative.  Softening enters as r.r + eps2.
+ *  - Vectors are n x 3 row-major FP64 arrays (x0 y0 z0 x1 y1 z1 ...).
+ *  - ptr_kind = SP2_HOST: every array argument of the call is host memory; the
+ *    call copies in, runs, copies out and returns when the results are in
+ *    place (synchronous).  ptr_kind = SP2_DEVICE: every array argument is
+ *    device memory of the context's GPU; the call only enqueues work on the
+ *    context's stream and returns (asynchronous; sp2_sync waits).
+ *  - Ownership: the caller owns every array it passes; the library never keeps
+ *    a caller pointer after a call returns.  The library owns its device copy
+ *    of the j-particles, the predicted records and its scratch space.
+ *  - Errors: every call returns an sp2_status; no exception or signal crosses
+ *    the ABI.  On error nothing is written to the outputs, and
+ *    sp2_last_error() returns a message.  A CUDA error makes the context
+ *    unusable (SP2_ERR_CUDA from every later call).
+ *  - Threads: a context is used by one host thread at a time.
+ *  - Self-interaction: the sink is itself a loaded j-particle (given by slot),
+ *    and the pair with itself is skipped.  Particle ids must be unique; the
+ *    nearest-neighbour output reports the neighbour's id.
+ *  - Precision: SP2_FP64 computes everything in IEEE double.  SP2_MIXED
+ *    predicts in FP64, stores positions as double-single (FP32 hi + lo) pairs,
+ *    forms x_j - x_i in double-single, evaluates rsqrt and the force terms in
+ *    FP32, and accumulates per-thread partial sums in FP32 that are flushed
+ *    into FP64 every tile; partial results of different j-slices are combined
+ *    in FP64.
+ */
+#ifndef SAPPORO_GB_H
+#define SAPPORO_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sp2_ctx sp2_ctx;
+typedef struct sp2_graph sp2_graph;
+typedef struct sp2_batch_plan sp2_batch_plan;
+
+typedef enum {
+    SP2_OK = 0,
+    SP2_ERR_ARG = -1,        /* null pointer, bad enum, negative size */
+    SP2_ERR_RANGE = -2,      /* size or index outside the context's capacity / loaded set */
+    SP2_ERR_NOMEM = -3,      /* device allocation failed */
+    SP2_ERR_CUDA = -4,       /* a CUDA runtime call or kernel failed */
+    SP2_ERR_STATE = -5,      /* call out of order (e.g. compute before predict) */
+    SP2_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up */
+    SP2_ERR_NONFINITE = -7,  /* the optional output scan found NaN or Inf */
+    SP2_ERR_UNSUPPORTED = -8 /* option not available in this configuration */
+} sp2_status;
+
+enum { SP2_FP64 = 0, SP2_MIXED = 1 };
+enum { SP2_HOST = 0, SP2_DEVICE = 1 };
+
+/* Optional device allocator (e.g. a caching allocator of the host program).
+ * alloc returns NULL on failure; free accepts what alloc returned. */
+typedef void *(*sp2_alloc_fn)(size_t bytes, void *user);
+typedef void (*sp2_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int order;            /* 4 (Hermite-4: acc, jerk, pot) or 6 (adds snap)            */
+    int precision;        /* SP2_FP64 or SP2_MIXED                                     */
+    int64_t n_max;        /* capacity: number of j-particle slots                      */
+    double eps2;          /* softening length squared, >= 0                            */
+    int with_nn;          /* 1: compute the nearest neighbour (id, r^2); 0: skip it     */
+    void *cuda_stream;    /* borrowed cudaStream_t, NULL: the library creates one      */
+    sp2_alloc_fn alloc;   /* NULL: cudaMalloc                                          */
+    sp2_free_fn free;     /* NULL: cudaFree                                            */
+    void *alloc_user;     /* passed to alloc / free                                    */
+    int profile;          /* 1: time each kernel with CUDA events (sp2_profile_read)   */
+    int check_finite;     /* 1: scan outputs for NaN/Inf after each compute (syncs)    */
+} sp2_config;
+
+/* Launch shape of the force kernel (the autotuner's search space). */
+typedef struct {
+    int threads;       /* threads per CTA: 32, 64, 128 or 256                         */
+    int i_per_thread;  /* sinks held by one thread: 1, 2 or 4                          */
+    int j_lanes;       /* threads sharing one sink, each taking every j_lanes-th source:
+                          1, 2, 4, ..., min(32, threads) (the paper's 2D blocks)  */
+    int j_tile;        /* sources staged in shared memory per pipeline stage          */
+    int split_j;       /* source slices processed independently, combined by the
+                          FP64 reduction kernel (1: no reduction pass)                */
+    int ctas_per_sm;   /* persistent-grid residency, 0 = occupancy maximum           */
+} sp2_launch;
+
+/* Fill *cfg with defaults: order 4, SP2_MIXED, n_max 0, eps2 0, with_nn 1, no
+ * borrowed stream, cudaMalloc, no profiling, no finite check. */
+void sp2_config_default(sp2_config *cfg);
+
+/* Create a context on the current CUDA device (Sec. 2.2: one particle store and
+ * its kernels per device).  Allocates the j store for cfg->n_max particles.
+ * Errors: SP2_ERR_ARG (order not 4/6, precision, n_max <= 0 or > 2^30,
+ * eps2 < 0 or not finite, alloc without free), SP2_ERR_NOMEM, SP2_ERR_CUDA. */
+sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg);
+
+/* Release everything the context owns (not a borrowed stream).  NULL is a no-op. */
+sp2_status sp2_close(sp2_ctx *ctx);
+
+/* Copy kernel (Sec. 2.2.4, "copy kernel"): store n j-particles.
+ *  slots == NULL: into slots first .. first+n-1 (first + n <= n_max); the loaded
+ *                 count becomes max(loaded, first + n).
+ *  slots != NULL: particle k goes to slot slots[k] (int32, each < loaded count;
+ *                 `first` is ignored); used to update the active particles of a
+ *                 block step.
+ * id[n] int32, m[n], x/v/a/jerk[n x 3], snap[n x 3] (order 6 only, else NULL),
+ * t[n] (time at which x, v, a, jerk, snap are valid).  Marks the predicted
+ * records stale.  Errors: SP2_ERR_ARG, SP2_ERR_RANGE. */
+sp2_status sp2_set_j(sp2_ctx *ctx, int64_t first, int64_t n, const int32_t *slots,
+                     const int32_t *id, const double *m, const double *x, const double *v,
+                     const double *a, const double *jerk, const double *snap,
+                     const double *t, int ptr_kind);
+
+/* Predictor (Sec. 2.2.4 "predict" kernel; Hermite predictor of Makino & Aarseth
+ * 1992 / Nitadori & Makino 2008): Taylor-expand every loaded j-particle from its
+ * own t_j to t and write the predicted records used by sp2_compute (FP64
+ * records, or double-single records in SP2_MIXED).  dt^k/k! is formed as
+ * dt^k times the double nearest 1/k!, sums left to right.
+ * Errors: SP2_ERR_STATE (nothing loaded), SP2_ERR_ARG (t not finite). */
+sp2_status sp2_predict(sp2_ctx *ctx, double t);
+
+/* Gravity kernel (Sec. 2.1 and 2.2.4): for each of the n_i sinks, given as
+ * slots i_idx[n_i] (int32) of the loaded set, sum over the sources in slots
+ * j_begin .. j_end-1 (sp2_compute: all loaded) except itself:
+ *   acc[n_i x 3], jerk[n_i x 3], snap[n_i x 3] (order 6; else pass NULL),
+ *   pot[n_i], nn_id[n_i] (int32, -1 when there is no other source),
+ *   nn_r2[n_i] (unsoftened squared distance, +inf when none).
+ * Any output may be NULL (not computed / not written); nn_* need with_nn.
+ * Sinks are the predicted j-particles at t.  The source range is split into
+ * slices over the whole GPU when n_i is small (Sec. 2.1, the source-split
+ * method), and the slices are combined by a deterministic FP64 reduction
+ * kernel.  Errors: SP2_ERR_STATE (records stale: call sp2_predict),
+ * SP2_ERR_RANGE (slot >= loaded count, bad range), SP2_ERR_ARG,
+ * SP2_ERR_NONFINITE (check_finite). n_i == 0 is a successful no-op. */
+sp2_status sp2_compute(sp2_ctx *ctx, int64_t n_i, const int32_t *i_idx,
+                       double *acc, double *jerk, double *snap, double *pot,
+                       int32_t *nn_id, double *nn_r2, int ptr_kind);
+sp2_status sp2_compute_range(sp2_ctx *ctx, int64_t j_begin, int64_t j_end,
+                             int64_t n_i, const int32_t *i_idx,
+                             double *acc, double *jerk, double *snap, double *pot,
+                             int32_t *nn_id, double *nn_r2, int ptr_kind);
+
+/* Many independent systems (the few-body / planetary regime of Sec. 2.1):
+ * system s owns the loaded slots offsets[s] .. offsets[s+1]-1 (host int64
+ * array of n_sys + 1 increasing entries, offsets[n_sys] <= loaded), every
+ * particle of every system is a sink, and only particles of the same system
+ * interact.  The plan orders the (system, 32-sink chunk) work items by cost for
+ * the persistent kernel's device-side work queue; build it once per set of
+ * system sizes.  Errors: SP2_ERR_ARG, SP2_ERR_RANGE (a system larger than
+ * 4096 particles, or offsets outside the loaded set). */
+sp2_status sp2_batch_plan_create(sp2_ctx *ctx, int64_t n_sys, const int64_t *offsets,
+                                 sp2_batch_plan **plan);
+sp2_status sp2_batch_plan_destroy(sp2_batch_plan *plan);
+/* Run the plan on the predicted records: outputs are indexed by slot - offsets[0]
+ * (length offsets[n_sys] - offsets[0]), layouts as sp2_compute. */
+sp2_status sp2_compute_batched(sp2_ctx *ctx, const sp2_batch_plan *plan,
+                               double *acc, double *jerk, double *snap, double *pot,
+                               int32_t *nn_id, double *nn_r2, int ptr_kind);
+
+/* All-pairs forces of n particles given directly (no store, no predictor): every
+ * particle is a sink and a source; m[n], x/v[n x 3] FP64; acc/jerk[n x 3],
+ * pot[n] (any output may be NULL).  Order-4 quantities.  This is the forward of
+ * the differentiable force below.  Uses the context's scratch (n <= n_max). */
+sp2_status sp2_forces(sp2_ctx *ctx, int64_t n, const double *m, const double *x,
+                      const double *v, double *acc, double *jerk, double *pot, int ptr_kind);
+
+/* Vector-Jacobian product of sp2_forces: given cotangents abar, jbar [n x 3] and
+ * pbar [n] (NULL = zero) of acc, jerk, pot, write
+ *   xbar = sum abar . dacc/dx + jbar . djerk/dx + pbar . dpot/dx   [n x 3]
+ *   vbar (same for v) [n x 3],  mbar [n].
+ * One pairwise pass in which each pair contributes through both of its ends.
+ * accumulate = 1 adds into xbar/vbar/mbar instead of overwriting. */
+sp2_status sp2_force_vjp(sp2_ctx *ctx, int64_t n, const double *m, const double *x,
+                         const double *v, const double *abar, const double *jbar,
+                         const double *pbar, double *xbar, double *vbar, double *mbar,
+                         int accumulate, int ptr_kind);
+
+/* One shared time-step of the 4th-order Hermite scheme (Makino & Aarseth 1992)
+ * on device arrays, in place: predict (x, v) with (a, jerk), evaluate acc and
+ * jerk there (sp2_forces), correct
+ *   v1 = v + (a + a1) dt/2 + (jerk - jerk1) dt^2/12
+ *   x1 = x + (v + v1) dt/2 + (a - a1) dt^2/12
+ * and leave (x1, v1, a1, jerk1).  Device pointers only. */
+sp2_status sp2_hermite4_step(sp2_ctx *ctx, int64_t n, double dt, const double *m,
+                             double *x, double *v, double *a, double *jerk);
+
+/* Reverse of sp2_hermite4_step.  x, v, a, jerk hold the step's INPUT state
+ * (unchanged).  On entry gx, gv, ga, gj hold the cotangents of the step's
+ * outputs; on return the cotangents of its inputs.  gm[n] is accumulated.
+ * The predicted state is recomputed.  Device pointers only. */
+sp2_status sp2_hermite4_step_vjp(sp2_ctx *ctx, int64_t n, double dt, const double *m,
+                                 const double *x, const double *v, const double *a,
+                                 const double *jerk, double *gx, double *gv, double *ga,
+                                 double *gj, double *gm);
+
+/* Launch-shape control.  sp2_autotune times candidate launch shapes for sink
+ * counts n_i on the current predicted records (Sec. 3.1: the block / thread
+ * configuration is tuned per GPU) and caches the best for that size bucket;
+ * sp2_get_launch reports what sp2_compute would use for n_i; sp2_set_launch
+ * overrides it for n_i's bucket (validated: SP2_ERR_ARG). */
+sp2_status sp2_autotune(sp2_ctx *ctx, int64_t n_i, sp2_launch *best);
+sp2_status sp2_get_launch(sp2_ctx *ctx, int64_t n_i, sp2_launch *out);
+sp2_status sp2_set_launch(sp2_ctx *ctx, int64_t n_i, const sp2_launch *in);
+
+/* CUDA-graph capture of a sequence of calls on the context's stream (device
+ * pointers only inside the capture; host-pointer calls return SP2_ERR_STATE).
+ * sp2_graph_launch replays the captured calls with the same pointers and
+ * arguments. */
+sp2_status sp2_graph_begin(sp2_ctx *ctx);
+sp2_status sp2_graph_end(sp2_ctx *ctx, sp2_graph **graph);
+sp2_status sp2_graph_launch(sp2_ctx *ctx, const sp2_graph *graph);
+sp2_status sp2_graph_destroy(sp2_graph *graph);
+
+/* Wait for all work of the context's stream. */
+sp2_status sp2_sync(sp2_ctx *ctx);
+
+/* With cfg.profile = 1 every kernel launch of the library is bracketed by CUDA
+ * events on the context's stream.  sp2_profile_read waits for the stream and
+ * returns, per stage (predict, force, reduce, batched, vjp, other; n_stages
+ * entries at most), the number of launches and their summed milliseconds since
+ * the last sp2_profile_reset (a stage keeps the last 4096 launches).  Events
+ * are not recorded while a graph is being captured. */
+sp2_status sp2_profile_reset(sp2_ctx *ctx);
+sp2_status sp2_profile_read(sp2_ctx *ctx, int64_t *counts, double *total_ms, int n_stages);
+
+/* Number of kernels the library has launched on this context since it opened
+ * (memset / memcpy nodes excluded). */
+int64_t sp2_kernel_launches(const sp2_ctx *ctx);
+
+/* Loaded j-particle count and capacity. */
+sp2_status sp2_info(const sp2_ctx *ctx, int64_t *n_loaded, int64_t *n_max, int *sm_count);
+
+const char *sp2_strerror(sp2_status s);
+/* Copy the context's last error message (NUL-terminated, truncated to len). */
+sp2_status sp2_last_error(const sp2_ctx *ctx, char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAPPORO_GB_H */

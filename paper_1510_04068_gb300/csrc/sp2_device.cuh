@@ -1,0 +1,839 @@
+// sp2_device.cuh -- device code of the pairwise passes: predicted-record
+// layouts, the two precision policies (double-single "mixed" and FP64), the
+// adjoint policies, and the persistent kernel skeleton with its work queue,
+// the split-j reduction and the batched few-body kernel.
+//
+// Method (Sec. 2.1 of the paper): one thread (or j_lanes threads, the paper's
+// 2D thread blocks) per sink, the sources of a slice streamed through shared
+// memory; when the sinks are few the sources are split into slices (the
+// source-split method) so that every SM has work, and a second kernel combines
+// the slices (Sec. 2.2.4 describes both that two-kernel form and an atomic
+// form; this library uses the deterministic two-kernel form).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sp2_internal.h"
+
+namespace sp2 {
+
+constexpr int kStages = 3;          // shared-memory pipeline depth
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxThreads = 256;
+
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+__device__ __forceinline__ double d_inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+// 16-byte asynchronous global->shared copy (L2 only), grouped and awaited per stage.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint4 f4bits(float a, float b, float c, float d) {
+    return make_uint4(__float_as_uint(a), __float_as_uint(b), __float_as_uint(c), __float_as_uint(d));
+}
+__device__ __forceinline__ uint4 d2bits(double a, double b) {
+    const unsigned long long x = static_cast<unsigned long long>(__double_as_longlong(a));
+    const unsigned long long y = static_cast<unsigned long long>(__double_as_longlong(b));
+    return make_uint4(static_cast<unsigned>(x), static_cast<unsigned>(x >> 32), static_cast<unsigned>(y),
+                      static_cast<unsigned>(y >> 32));
+}
+
+// Lexicographic (r2, id) minimum; id -1 means "none" and only pairs with r2 = +inf.
+__device__ __forceinline__ void nn_merge(double &d, int &id, double od, int oid) {
+    if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) {
+        d = od;
+        id = oid;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision force policy: positions as double-single (hi + lo FP32),
+// x_j - x_i formed as (hi_j - hi_i) + (lo_j - lo_i); rsqrt (SFU) and all terms
+// in FP32; per-thread FP32 partial sums flushed into FP64 totals every kFlush
+// sources.
+// ---------------------------------------------------------------------------
+template <int ORDER, bool NN>
+struct MixedForce {
+    static constexpr int NW = (ORDER == 6) ? 4 : 3;  // 16-byte words per record
+    static constexpr int RB = NW * 16;
+    static constexpr int NS = (ORDER == 6) ? 10 : 7;  // summed fields
+    static constexpr bool kNN = NN;
+    static constexpr int kFlush = 64;
+    typedef float real;
+    struct Rec {
+        float4 w[NW];
+    };
+    struct Sink {
+        float xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;
+        int slot;
+    };
+    struct Acc {
+        float ax, ay, az, jx, jy, jz, sx, sy, sz, pot;
+        double Ax, Ay, Az, Jx, Jy, Jz, Sx, Sy, Sz, Pot;
+        float nn_d2;
+        int nn_j;
+    };
+
+    __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = *reinterpret_cast<const float4 *>(p + 16 * w);
+        return r;
+    }
+    __device__ static __forceinline__ Rec ld_global(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = __ldg(reinterpret_cast<const float4 *>(p) + w);
+        return r;
+    }
+    // Far-away, massless filler for the ragged end of a tile: its terms are
+    // exactly zero and its r^2 overflows to +inf (never a neighbour).
+    __device__ static __forceinline__ uint4 sentinel(int w) {
+        if (w == 0) return f4bits(1e25f, 1e25f, 1e25f, 0.f);
+        if (w == 1) return make_uint4(0u, 0u, 0u, 0xffffffffu);
+        return make_uint4(0u, 0u, 0u, 0u);
+    }
+    __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
+        const Rec r = ld_global(rec + slot * RB);
+        s.xh = r.w[0].x; s.yh = r.w[0].y; s.zh = r.w[0].z;
+        s.xl = r.w[1].x; s.yl = r.w[1].y; s.zl = r.w[1].z;
+        s.vx = r.w[2].x; s.vy = r.w[2].y; s.vz = r.w[2].z;
+        if (ORDER == 6) { s.ax = r.w[3].x; s.ay = r.w[3].y; s.az = r.w[3].z; }
+        else { s.ax = s.ay = s.az = 0.f; }
+    }
+    __device__ static __forceinline__ void init(Acc &c) {
+        c.ax = c.ay = c.az = c.jx = c.jy = c.jz = c.sx = c.sy = c.sz = c.pot = 0.f;
+        c.Ax = c.Ay = c.Az = c.Jx = c.Jy = c.Jz = c.Sx = c.Sy = c.Sz = c.Pot = 0.0;
+        c.nn_d2 = f_inf();
+        c.nn_j = -1;
+    }
+    template <bool SELF>
+    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, float eps2) {
+        const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
+        const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
+        const float dz = (r.w[0].z - s.zh) + (r.w[1].z - s.zl);
+        const float dvx = r.w[2].x - s.vx, dvy = r.w[2].y - s.vy, dvz = r.w[2].z - s.vz;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        float rinv = rsqrtf(d2 + eps2);
+        if (SELF && j == s.slot) rinv = 0.f;
+        const float rinv2 = rinv * rinv;
+        const float mr = r.w[0].w * rinv;
+        const float mr3 = mr * rinv2;
+        c.pot += mr;
+        const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
+        const float al3 = 3.f * (rv * rinv2);
+        if (ORDER == 4) {
+            c.ax = fmaf(mr3, dx, c.ax);
+            c.ay = fmaf(mr3, dy, c.ay);
+            c.az = fmaf(mr3, dz, c.az);
+            c.jx = fmaf(mr3, fmaf(-al3, dx, dvx), c.jx);
+            c.jy = fmaf(mr3, fmaf(-al3, dy, dvy), c.jy);
+            c.jz = fmaf(mr3, fmaf(-al3, dz, dvz), c.jz);
+        } else {
+            const float dax = r.w[3].x - s.ax, day = r.w[3].y - s.ay, daz = r.w[3].z - s.az;
+            const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
+            const float Jx = fmaf(-al3, Ax, mr3 * dvx);
+            const float Jy = fmaf(-al3, Ay, mr3 * dvy);
+            const float Jz = fmaf(-al3, Az, mr3 * dvz);
+            const float vv = fmaf(dvz, dvz, fmaf(dvy, dvy, dvx * dvx));
+            const float ra = fmaf(dz, daz, fmaf(dy, day, dx * dax));
+            const float al = rv * rinv2;
+            const float b3 = 3.f * fmaf(vv + ra, rinv2, al * al);
+            const float a6 = 2.f * al3;
+            c.ax += Ax; c.ay += Ay; c.az += Az;
+            c.jx += Jx; c.jy += Jy; c.jz += Jz;
+            c.sx += fmaf(mr3, dax, -fmaf(a6, Jx, b3 * Ax));
+            c.sy += fmaf(mr3, day, -fmaf(a6, Jy, b3 * Ay));
+            c.sz += fmaf(mr3, daz, -fmaf(a6, Jz, b3 * Az));
+        }
+        if (NN) {
+            const float dn = (SELF && j == s.slot) ? f_inf() : d2;
+            if (dn < c.nn_d2) { c.nn_d2 = dn; c.nn_j = j; }
+        }
+    }
+    __device__ static __forceinline__ void flush(Acc &c) {
+        c.Ax += c.ax; c.Ay += c.ay; c.Az += c.az;
+        c.Jx += c.jx; c.Jy += c.jy; c.Jz += c.jz;
+        if (ORDER == 6) { c.Sx += c.sx; c.Sy += c.sy; c.Sz += c.sz; }
+        c.Pot += c.pot;
+        c.ax = c.ay = c.az = c.jx = c.jy = c.jz = c.sx = c.sy = c.sz = c.pot = 0.f;
+    }
+    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
+        t[0] = c.Ax; t[1] = c.Ay; t[2] = c.Az;
+        t[3] = c.Jx; t[4] = c.Jy; t[5] = c.Jz;
+        if (ORDER == 6) { t[6] = c.Sx; t[7] = c.Sy; t[8] = c.Sz; t[9] = -c.Pot; }
+        else { t[6] = -c.Pot; }
+    }
+    // limit: one past the last real source slot (filler records never qualify,
+    // the bound keeps the id lookup inside the record array regardless).
+    __device__ static __forceinline__ void nn(const Acc &c, const unsigned char *rec, int64_t limit, double &d,
+                                              int &id) {
+        if (NN && c.nn_j >= 0 && c.nn_j < limit) {
+            d = static_cast<double>(c.nn_d2);
+            id = __ldg(reinterpret_cast<const int *>(rec + static_cast<int64_t>(c.nn_j) * RB + 28));
+        } else {
+            d = d_inf();
+            id = -1;
+        }
+    }
+    template <class Out>
+    __device__ static __forceinline__ void write_final(const Out &o, int64_t i, const double *t, double d, int id) {
+        if (o.acc) { o.acc[3 * i] = t[0]; o.acc[3 * i + 1] = t[1]; o.acc[3 * i + 2] = t[2]; }
+        if (o.jerk) { o.jerk[3 * i] = t[3]; o.jerk[3 * i + 1] = t[4]; o.jerk[3 * i + 2] = t[5]; }
+        if (ORDER == 6 && o.snap) { o.snap[3 * i] = t[6]; o.snap[3 * i + 1] = t[7]; o.snap[3 * i + 2] = t[8]; }
+        if (o.pot) o.pot[i] = t[NS - 1];
+        if (NN) {
+            if (o.nn_id) o.nn_id[i] = id;
+            if (o.nn_r2) o.nn_r2[i] = (id < 0) ? d_inf() : d;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// FP64 force policy: every operation in IEEE double.  The unsoftened r^2 is
+// formed without fused multiply-adds, so that nearest-neighbour decisions are
+// taken on exactly the values a plain FP64 evaluation produces.
+// ---------------------------------------------------------------------------
+template <int ORDER, bool NN>
+struct Fp64Force {
+    static constexpr int NW = (ORDER == 6) ? 6 : 4;
+    static constexpr int RB = NW * 16;
+    static constexpr int NS = (ORDER == 6) ? 10 : 7;
+    static constexpr bool kNN = NN;
+    static constexpr int kFlush = 1 << 30;
+    typedef double real;
+    struct Rec {
+        double2 w[NW];
+    };
+    struct Sink {
+        double x, y, z, vx, vy, vz, ax, ay, az;
+        int slot;
+    };
+    struct Acc {
+        double ax, ay, az, jx, jy, jz, sx, sy, sz, pot;
+        double nn_d2;
+        int nn_id;
+    };
+    __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = *reinterpret_cast<const double2 *>(p + 16 * w);
+        return r;
+    }
+    __device__ static __forceinline__ Rec ld_global(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = __ldg(reinterpret_cast<const double2 *>(p) + w);
+        return r;
+    }
+    __device__ static __forceinline__ uint4 sentinel(int w) {
+        if (w == 0) return d2bits(1e200, 1e200);
+        if (w == 1) return d2bits(1e200, 0.0);
+        if (w == 3) return make_uint4(0u, 0u, 0xffffffffu, 0xffffffffu);
+        return make_uint4(0u, 0u, 0u, 0u);
+    }
+    __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
+        const Rec r = ld_global(rec + slot * RB);
+        s.x = r.w[0].x; s.y = r.w[0].y; s.z = r.w[1].x;
+        s.vx = r.w[2].x; s.vy = r.w[2].y; s.vz = r.w[3].x;
+        if (ORDER == 6) { s.ax = r.w[4].x; s.ay = r.w[4].y; s.az = r.w[5].x; }
+        else { s.ax = s.ay = s.az = 0.0; }
+    }
+    __device__ static __forceinline__ void init(Acc &c) {
+        c.ax = c.ay = c.az = c.jx = c.jy = c.jz = c.sx = c.sy = c.sz = c.pot = 0.0;
+        c.nn_d2 = d_inf();
+        c.nn_id = -1;
+    }
+    template <bool SELF>
+    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, double eps2) {
+        const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
+        const double m = r.w[1].y;
+        const double dvx = r.w[2].x - s.vx, dvy = r.w[2].y - s.vy, dvz = r.w[3].x - s.vz;
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        double rinv = rsqrt(d2 + eps2);
+        if (SELF && j == s.slot) rinv = 0.0;
+        const double rinv2 = rinv * rinv;
+        const double mr = m * rinv;
+        const double mr3 = mr * rinv2;
+        c.pot -= mr;
+        const double Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
+        const double rv = dx * dvx + dy * dvy + dz * dvz;
+        const double al = rv * rinv2;
+        const double Jx = mr3 * dvx - 3.0 * al * Ax;
+        const double Jy = mr3 * dvy - 3.0 * al * Ay;
+        const double Jz = mr3 * dvz - 3.0 * al * Az;
+        c.ax += Ax; c.ay += Ay; c.az += Az;
+        c.jx += Jx; c.jy += Jy; c.jz += Jz;
+        if (ORDER == 6) {
+            const double dax = r.w[4].x - s.ax, day = r.w[4].y - s.ay, daz = r.w[5].x - s.az;
+            const double vv = dvx * dvx + dvy * dvy + dvz * dvz;
+            const double ra = dx * dax + dy * day + dz * daz;
+            const double beta = (vv + ra) * rinv2 + al * al;
+            c.sx += mr3 * dax - 6.0 * al * Jx - 3.0 * beta * Ax;
+            c.sy += mr3 * day - 6.0 * al * Jy - 3.0 * beta * Ay;
+            c.sz += mr3 * daz - 6.0 * al * Jz - 3.0 * beta * Az;
+        }
+        if (NN) {
+            const int id = static_cast<int>(__double_as_longlong(r.w[3].y));
+            const bool self = SELF && j == s.slot;
+            if (!self && (d2 < c.nn_d2 || (d2 == c.nn_d2 && id < c.nn_id))) {
+                c.nn_d2 = d2;
+                c.nn_id = id;
+            }
+        }
+    }
+    __device__ static __forceinline__ void flush(Acc &) {}
+    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
+        t[0] = c.ax; t[1] = c.ay; t[2] = c.az;
+        t[3] = c.jx; t[4] = c.jy; t[5] = c.jz;
+        if (ORDER == 6) { t[6] = c.sx; t[7] = c.sy; t[8] = c.sz; t[9] = c.pot; }
+        else { t[6] = c.pot; }
+    }
+    __device__ static __forceinline__ void nn(const Acc &c, const unsigned char *, int64_t, double &d, int &id) {
+        d = c.nn_d2;
+        id = NN ? c.nn_id : -1;
+        if (id < 0) d = d_inf();
+    }
+    template <class Out>
+    __device__ static __forceinline__ void write_final(const Out &o, int64_t i, const double *t, double d, int id) {
+        MixedForce<ORDER, NN>::write_final(o, i, t, d, id);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Adjoint policies.  For a pair (sink k, source l) with r = x_l - x_k,
+// v = v_l - v_k, s = (r.r + eps^2)^-1/2, alpha = (r.v) s^2, q = m_l s^3 and
+// the sink's cotangents (abar, jbar, pbar) of (acc, jerk, pot), the scalar
+//   L = abar.A + jbar.J + pbar.phi = q (abar.r + jbar.v - 3 alpha jbar.r) - pbar m_l s
+// has the gradients
+//   dL/dr = q abar - 3 q alpha jbar - 3 q s^2 (jbar.r) v
+//           + r [ -3 q s^2 B + 6 q alpha s^2 (jbar.r) + pbar m_l s^3 ],  B = abar.r + jbar.v - 3 alpha jbar.r
+//   dL/dv = q (jbar - 3 s^2 (jbar.r) r)
+//   dL/dm_l = s^3 B - pbar s.
+// Particle k collects -dL/dr, -dL/dv of its own sink sums and +dL/dr, +dL/dv,
+// +dL/dm of every other sink's sums in which it is the source, in one pass.
+// ---------------------------------------------------------------------------
+struct MixedVjp {
+    static constexpr int NW = 5;
+    static constexpr int RB = 80;
+    static constexpr int NS = 7;
+    static constexpr bool kNN = false;
+    static constexpr int kFlush = 64;
+    typedef float real;
+    struct Rec {
+        float4 w[NW];
+    };
+    struct Sink {
+        float xh, yh, zh, xl, yl, zl, vx, vy, vz, abx, aby, abz, jbx, jby, jbz, pb, m;
+        int slot;
+    };
+    struct Acc {
+        float gx, gy, gz, hx, hy, hz, gm;
+        double Gx, Gy, Gz, Hx, Hy, Hz, Gm;
+    };
+    __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = *reinterpret_cast<const float4 *>(p + 16 * w);
+        return r;
+    }
+    __device__ static __forceinline__ Rec ld_global(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = __ldg(reinterpret_cast<const float4 *>(p) + w);
+        return r;
+    }
+    __device__ static __forceinline__ uint4 sentinel(int w) {
+        if (w == 0) return f4bits(1e25f, 1e25f, 1e25f, 0.f);
+        return make_uint4(0u, 0u, 0u, 0u);
+    }
+    __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
+        const Rec r = ld_global(rec + slot * RB);
+        s.xh = r.w[0].x; s.yh = r.w[0].y; s.zh = r.w[0].z; s.m = r.w[0].w;
+        s.xl = r.w[1].x; s.yl = r.w[1].y; s.zl = r.w[1].z; s.pb = r.w[1].w;
+        s.vx = r.w[2].x; s.vy = r.w[2].y; s.vz = r.w[2].z;
+        s.abx = r.w[3].x; s.aby = r.w[3].y; s.abz = r.w[3].z;
+        s.jbx = r.w[4].x; s.jby = r.w[4].y; s.jbz = r.w[4].z;
+    }
+    __device__ static __forceinline__ void init(Acc &c) {
+        c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.f;
+        c.Gx = c.Gy = c.Gz = c.Hx = c.Hy = c.Hz = c.Gm = 0.0;
+    }
+    template <bool SELF>
+    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, float eps2) {
+        const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
+        const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
+        const float dz = (r.w[0].z - s.zh) + (r.w[1].z - s.zl);
+        const float vx = r.w[2].x - s.vx, vy = r.w[2].y - s.vy, vz = r.w[2].z - s.vz;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        float rinv = rsqrtf(d2 + eps2);
+        if (SELF && j == s.slot) rinv = 0.f;
+        const float s2 = rinv * rinv, s3 = rinv * s2;
+        const float al = fmaf(dz, vz, fmaf(dy, vy, dx * vx)) * s2;
+        const float ml = r.w[0].w, pl = r.w[1].w;
+        const float abx = r.w[3].x, aby = r.w[3].y, abz = r.w[3].z;
+        const float jbx = r.w[4].x, jby = r.w[4].y, jbz = r.w[4].z;
+        // sink-side sums (cotangents of k) and source-side sums (cotangents of l)
+        const float jr1 = fmaf(s.jbz, dz, fmaf(s.jby, dy, s.jbx * dx));
+        const float B1 = fmaf(s.abz, dz, fmaf(s.aby, dy, s.abx * dx)) + fmaf(s.jbz, vz, fmaf(s.jby, vy, s.jbx * vx)) - 3.f * al * jr1;
+        const float jr2 = fmaf(jbz, dz, fmaf(jby, dy, jbx * dx));
+        const float B2 = fmaf(abz, dz, fmaf(aby, dy, abx * dx)) + fmaf(jbz, vz, fmaf(jby, vy, jbx * vx)) - 3.f * al * jr2;
+        const float q1 = ml * s3, q2 = s.m * s3;
+        const float D = q1 * jr1 - q2 * jr2;
+        const float cv = 3.f * s2 * D;
+        const float cr = 3.f * s2 * (q1 * B1 - q2 * B2) - 6.f * al * s2 * D - s3 * fmaf(s.pb, ml, pl * s.m);
+        const float t1 = 3.f * al * q1, t2 = 3.f * al * q2;
+        c.gx += q2 * abx - q1 * s.abx + t1 * s.jbx - t2 * jbx + cv * vx + cr * dx;
+        c.gy += q2 * aby - q1 * s.aby + t1 * s.jby - t2 * jby + cv * vy + cr * dy;
+        c.gz += q2 * abz - q1 * s.abz + t1 * s.jbz - t2 * jbz + cv * vz + cr * dz;
+        c.hx += q2 * jbx - q1 * s.jbx + cv * dx;
+        c.hy += q2 * jby - q1 * s.jby + cv * dy;
+        c.hz += q2 * jbz - q1 * s.jbz + cv * dz;
+        c.gm -= fmaf(s3, B2, pl * rinv);
+    }
+    __device__ static __forceinline__ void flush(Acc &c) {
+        c.Gx += c.gx; c.Gy += c.gy; c.Gz += c.gz;
+        c.Hx += c.hx; c.Hy += c.hy; c.Hz += c.hz;
+        c.Gm += c.gm;
+        c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.f;
+    }
+    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
+        t[0] = c.Gx; t[1] = c.Gy; t[2] = c.Gz; t[3] = c.Hx; t[4] = c.Hy; t[5] = c.Hz; t[6] = c.Gm;
+    }
+    __device__ static __forceinline__ void nn(const Acc &, const unsigned char *, int64_t, double &d, int &id) {
+        d = d_inf();
+        id = -1;
+    }
+    template <class Out>
+    __device__ static __forceinline__ void write_final(const Out &o, int64_t i, const double *t, double, int) {
+        if (o.accumulate) {
+            o.xbar[3 * i] += t[0]; o.xbar[3 * i + 1] += t[1]; o.xbar[3 * i + 2] += t[2];
+            o.vbar[3 * i] += t[3]; o.vbar[3 * i + 1] += t[4]; o.vbar[3 * i + 2] += t[5];
+            o.mbar[i] += t[6];
+        } else {
+            o.xbar[3 * i] = t[0]; o.xbar[3 * i + 1] = t[1]; o.xbar[3 * i + 2] = t[2];
+            o.vbar[3 * i] = t[3]; o.vbar[3 * i + 1] = t[4]; o.vbar[3 * i + 2] = t[5];
+            o.mbar[i] = t[6];
+        }
+    }
+};
+
+struct Fp64Vjp {
+    static constexpr int NW = 7;
+    static constexpr int RB = 112;
+    static constexpr int NS = 7;
+    static constexpr bool kNN = false;
+    static constexpr int kFlush = 1 << 30;
+    typedef double real;
+    struct Rec {
+        double2 w[NW];
+    };
+    struct Sink {
+        double x, y, z, vx, vy, vz, abx, aby, abz, jbx, jby, jbz, pb, m;
+        int slot;
+    };
+    struct Acc {
+        double gx, gy, gz, hx, hy, hz, gm;
+    };
+    __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = *reinterpret_cast<const double2 *>(p + 16 * w);
+        return r;
+    }
+    __device__ static __forceinline__ Rec ld_global(const unsigned char *p) {
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = __ldg(reinterpret_cast<const double2 *>(p) + w);
+        return r;
+    }
+    __device__ static __forceinline__ uint4 sentinel(int w) {
+        if (w == 0) return d2bits(1e200, 1e200);
+        if (w == 1) return d2bits(1e200, 0.0);
+        return make_uint4(0u, 0u, 0u, 0u);
+    }
+    __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
+        const Rec r = ld_global(rec + slot * RB);
+        s.x = r.w[0].x; s.y = r.w[0].y; s.z = r.w[1].x; s.m = r.w[1].y;
+        s.vx = r.w[2].x; s.vy = r.w[2].y; s.vz = r.w[3].x; s.pb = r.w[3].y;
+        s.abx = r.w[4].x; s.aby = r.w[4].y; s.abz = r.w[5].x;
+        s.jbx = r.w[5].y; s.jby = r.w[6].x; s.jbz = r.w[6].y;
+    }
+    __device__ static __forceinline__ void init(Acc &c) { c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.0; }
+    template <bool SELF>
+    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, double eps2) {
+        const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
+        const double vx = r.w[2].x - s.vx, vy = r.w[2].y - s.vy, vz = r.w[3].x - s.vz;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        double rinv = rsqrt(d2 + eps2);
+        if (SELF && j == s.slot) rinv = 0.0;
+        const double s2 = rinv * rinv, s3 = rinv * s2;
+        const double al = (dx * vx + dy * vy + dz * vz) * s2;
+        const double ml = r.w[1].y, pl = r.w[3].y;
+        const double abx = r.w[4].x, aby = r.w[4].y, abz = r.w[5].x;
+        const double jbx = r.w[5].y, jby = r.w[6].x, jbz = r.w[6].y;
+        const double jr1 = s.jbx * dx + s.jby * dy + s.jbz * dz;
+        const double B1 = s.abx * dx + s.aby * dy + s.abz * dz + s.jbx * vx + s.jby * vy + s.jbz * vz - 3.0 * al * jr1;
+        const double jr2 = jbx * dx + jby * dy + jbz * dz;
+        const double B2 = abx * dx + aby * dy + abz * dz + jbx * vx + jby * vy + jbz * vz - 3.0 * al * jr2;
+        const double q1 = ml * s3, q2 = s.m * s3;
+        const double D = q1 * jr1 - q2 * jr2;
+        const double cv = 3.0 * s2 * D;
+        const double cr = 3.0 * s2 * (q1 * B1 - q2 * B2) - 6.0 * al * s2 * D - s3 * (s.pb * ml + pl * s.m);
+        const double t1 = 3.0 * al * q1, t2 = 3.0 * al * q2;
+        c.gx += q2 * abx - q1 * s.abx + t1 * s.jbx - t2 * jbx + cv * vx + cr * dx;
+        c.gy += q2 * aby - q1 * s.aby + t1 * s.jby - t2 * jby + cv * vy + cr * dy;
+        c.gz += q2 * abz - q1 * s.abz + t1 * s.jbz - t2 * jbz + cv * vz + cr * dz;
+        c.hx += q2 * jbx - q1 * s.jbx + cv * dx;
+        c.hy += q2 * jby - q1 * s.jby + cv * dy;
+        c.hz += q2 * jbz - q1 * s.jbz + cv * dz;
+        c.gm -= s3 * B2 + pl * rinv;
+    }
+    __device__ static __forceinline__ void flush(Acc &) {}
+    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
+        t[0] = c.gx; t[1] = c.gy; t[2] = c.gz; t[3] = c.hx; t[4] = c.hy; t[5] = c.hz; t[6] = c.gm;
+    }
+    __device__ static __forceinline__ void nn(const Acc &, const unsigned char *, int64_t, double &d, int &id) {
+        d = d_inf();
+        id = -1;
+    }
+    template <class Out>
+    __device__ static __forceinline__ void write_final(const Out &o, int64_t i, const double *t, double d, int id) {
+        MixedVjp::write_final(o, i, t, d, id);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Persistent pass kernel.  Work item = (i-block, j-slice); CTAs fetch items
+// from a device counter (atomicAdd, no waiting).  Sources of the slice stream
+// through a kStages-deep ring of shared-memory tiles filled with 16-byte
+// cp.async copies; the ragged end of the last tile is filled with sentinel
+// records so the inner loop has a fixed trip count.  Sinks whose own slot lies
+// in the current tile take the variant of the loop that skips the self pair.
+// ---------------------------------------------------------------------------
+template <class P>
+__device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *smem, int t, int64_t j0, int64_t j1) {
+    const int tile = p.tile;
+    unsigned char *dst = smem + static_cast<size_t>(t % kStages) * tile * P::RB;
+    const int64_t tb = j0 + static_cast<int64_t>(t) * tile;
+    const int64_t rem = j1 - tb;
+    const int cnt = rem < tile ? static_cast<int>(rem) : tile;
+    const unsigned char *src = p.rec + tb * P::RB;
+    constexpr int W = P::RB / 16;
+    const int n16 = tile * W, v16 = cnt * W;
+    for (int c = threadIdx.x; c < n16; c += blockDim.x) {
+        if (c < v16) cp_async16(dst + 16 * c, src + 16 * static_cast<size_t>(c));
+        else *reinterpret_cast<uint4 *>(dst + 16 * c) = P::sentinel(c % W);
+    }
+}
+
+template <class P, int IPT, bool SELF>
+__device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int per, int jl, int lj,
+                                          const typename P::Sink *sk, typename P::Acc *ac,
+                                          typename P::real eps2) {
+    const unsigned char *base = st + lj * P::RB;
+    const int step = jl * P::RB;
+#pragma unroll 4
+    for (int q = 0; q < per; ++q) {
+        const typename P::Rec r = P::ld_shared(base + q * step);
+        const int j = tb + q * jl + lj;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) P::template interact<SELF>(r, j, sk[k], ac[k], eps2);
+    }
+}
+
+template <class P, int IPT>
+__global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned int s_item;
+    const int tid = threadIdx.x;
+    const int jl = p.jl;
+    const int lj = tid & (jl - 1);
+    const int islot = tid / jl;
+    const int slots = blockDim.x / jl;
+    const typename P::real eps2 = static_cast<typename P::real>(p.eps2);
+    const int per = p.tile / jl;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(p.queue, 1u);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= p.n_items) break;
+        const int64_t iblk = item % p.n_iblk;
+        const int slice = static_cast<int>(item / p.n_iblk);
+
+        typename P::Sink sk[IPT];
+        typename P::Acc ac[IPT];
+        bool val[IPT];
+        int64_t ii[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            ii[k] = iblk * p.sinks_per_cta + static_cast<int64_t>(k) * slots + islot;
+            val[k] = ii[k] < p.n_i;
+            const int raw = val[k] ? __ldg(p.i_idx + ii[k]) : 0;
+            if (val[k] && (raw < 0 || raw >= p.n_loaded)) {
+                atomicOr(p.err, 1u);  // reported by sp2_sync; this sink is skipped
+                val[k] = false;
+            }
+            const int slot = val[k] ? raw : static_cast<int>(p.j_begin);
+            P::load_sink(p.rec, slot, sk[k]);
+            sk[k].slot = val[k] ? slot : -1;
+            P::init(ac[k]);
+        }
+        const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
+        const int64_t j1 = (j0 + p.slice_len < p.j_end) ? j0 + p.slice_len : p.j_end;
+        const int n_tiles = static_cast<int>((j1 - j0 + p.tile - 1) / p.tile);
+
+#pragma unroll
+        for (int s = 0; s < kStages - 1; ++s) {
+            if (s < n_tiles) load_tile<P>(p, smem, s, j0, j1);
+            cp_async_commit();
+        }
+        int since_flush = 0;
+        for (int t = 0; t < n_tiles; ++t) {
+            cp_async_wait<kStages - 2>();
+            __syncthreads();
+            if (t + kStages - 1 < n_tiles) load_tile<P>(p, smem, t + kStages - 1, j0, j1);
+            cp_async_commit();
+            const unsigned char *st = smem + static_cast<size_t>(t % kStages) * p.tile * P::RB;
+            const int tb = static_cast<int>(j0) + t * p.tile;
+            const int te = (tb + p.tile < j1) ? tb + p.tile : static_cast<int>(j1);
+            bool mine = false;
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) mine |= (sk[k].slot >= tb) && (sk[k].slot < te);
+            if (__any_sync(kFull, mine)) tile_loop<P, IPT, true>(st, tb, per, jl, lj, sk, ac, eps2);
+            else tile_loop<P, IPT, false>(st, tb, per, jl, lj, sk, ac, eps2);
+            since_flush += per;
+            if (since_flush >= P::kFlush) {
+#pragma unroll
+                for (int k = 0; k < IPT; ++k) P::flush(ac[k]);
+                since_flush = 0;
+            }
+        }
+        cp_async_wait<0>();
+
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            P::flush(ac[k]);
+            double t[P::NS];
+            P::totals(ac[k], t);
+            double nd;
+            int nid;
+            P::nn(ac[k], p.rec, p.j_end, nd, nid);
+            for (int off = jl >> 1; off > 0; off >>= 1) {
+#pragma unroll
+                for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+                if (P::kNN) {
+                    const double od = __shfl_xor_sync(kFull, nd, off);
+                    const int oid = __shfl_xor_sync(kFull, nid, off);
+                    nn_merge(nd, nid, od, oid);
+                }
+            }
+            if (lj == 0 && val[k]) {
+                if (p.split == 1) {
+                    P::write_final(p, ii[k], t, nd, nid);
+                } else {
+                    const int64_t stride = static_cast<int64_t>(p.split) * p.n_i;
+                    double *base = p.part + static_cast<int64_t>(slice) * p.n_i + ii[k];
+#pragma unroll
+                    for (int f = 0; f < P::NS; ++f) base[f * stride] = t[f];
+                    if (P::kNN) {
+                        base[P::NS * stride] = nd;
+                        p.part_id[static_cast<int64_t>(slice) * p.n_i + ii[k]] = nid;
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// Second kernel of the source split: sum the slices of each sink in slice
+// order (deterministic, FP64) and take the lexicographic (r2, id) minimum.
+template <class P>
+__global__ void reduce_kernel(const ReduceParams r) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= r.n_i) return;
+    const int64_t stride = static_cast<int64_t>(r.split) * r.n_i;
+    double t[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    double nd = d_inf();
+    int nid = -1;
+    for (int s = 0; s < r.split; ++s) {
+        const double *base = r.part + static_cast<int64_t>(s) * r.n_i + i;
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] += base[f * stride];
+        if (P::kNN) nn_merge(nd, nid, base[P::NS * stride], r.part_id[static_cast<int64_t>(s) * r.n_i + i]);
+    }
+    P::write_final(r, i, t, nd, nid);
+}
+
+// The same reduction with one warp per sink, for many slices (small n_i): lane
+// l sums slices l, l+32, ... in order, then a fixed xor-butterfly combines the
+// lanes, so the result is still independent of scheduling.
+template <class P>
+__global__ void reduce_warp_kernel(const ReduceParams r) {
+    const int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= r.n_i) return;  // uniform across the warp
+    const int64_t stride = static_cast<int64_t>(r.split) * r.n_i;
+    double t[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    double nd = d_inf();
+    int nid = -1;
+    for (int s = lane; s < r.split; s += 32) {
+        const double *base = r.part + static_cast<int64_t>(s) * r.n_i + i;
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] += base[f * stride];
+        if (P::kNN) nn_merge(nd, nid, base[P::NS * stride], r.part_id[static_cast<int64_t>(s) * r.n_i + i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+        if (P::kNN) {
+            const double od = __shfl_xor_sync(kFull, nd, off);
+            const int oid = __shfl_xor_sync(kFull, nid, off);
+            nn_merge(nd, nid, od, oid);
+        }
+    }
+    if (lane == 0) P::write_final(r, i, t, nd, nid);
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernel for many small independent systems: persistent warps, each
+// fetching (system, up-to-32-sink chunk) items from the device work queue in
+// the plan's cost order; one sink per lane, the system's sources read with
+// warp-uniform (broadcast) loads that stay in L1 while the chunks of one
+// system are processed.
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams b) {
+    const int lane = threadIdx.x & 31;
+    const typename P::real eps2 = static_cast<typename P::real>(b.eps2);
+    for (;;) {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(b.queue, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= b.n_items) break;
+        const int4 it = __ldg(b.items + item);  // {system first slot, size, chunk first slot, chunk size}
+        const bool val = lane < it.w;
+        const int slot = it.z + (val ? lane : 0);
+        typename P::Sink sk;
+        typename P::Acc ac;
+        P::load_sink(b.rec, slot, sk);
+        sk.slot = val ? slot : -1;
+        P::init(ac);
+        const unsigned char *src = b.rec + static_cast<int64_t>(it.x) * P::RB;
+        int since = 0;
+#pragma unroll 4
+        for (int q = 0; q < it.y; ++q) {
+            const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
+            P::template interact<true>(r, it.x + q, sk, ac, eps2);
+            if (++since == P::kFlush) { P::flush(ac); since = 0; }
+        }
+        P::flush(ac);
+        double t[P::NS];
+        P::totals(ac, t);
+        double nd;
+        int nid;
+        P::nn(ac, b.rec, static_cast<int64_t>(it.x) + it.y, nd, nid);
+        if (val) P::write_final(b, static_cast<int64_t>(slot) - b.out_base, t, nd, nid);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Instantiation helpers for one (order, precision) translation unit.
+// ---------------------------------------------------------------------------
+template <class P, int IPT>
+inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t smem, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    pass_kernel<P, IPT><<<grid, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <class P, int IPT>
+inline cudaError_t occupancy_pass(int threads, size_t smem, int *blocks) {
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT>, threads, smem);
+}
+
+template <class P>
+inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t smem,
+                                cudaStream_t s, int *blocks) {
+    switch (ipt) {
+        case 1: return occ ? occupancy_pass<P, 1>(threads, smem, blocks) : launch_pass<P, 1>(*p, grid, threads, smem, s);
+        case 2: return occ ? occupancy_pass<P, 2>(threads, smem, blocks) : launch_pass<P, 2>(*p, grid, threads, smem, s);
+        case 4: return occ ? occupancy_pass<P, 4>(threads, smem, blocks) : launch_pass<P, 4>(*p, grid, threads, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class P>
+inline cudaError_t launch_reduce(const ReduceParams &r, cudaStream_t s) {
+    const int threads = 256;
+    if (r.split >= 32) {
+        const int64_t grid = (32 * r.n_i + threads - 1) / threads;
+        reduce_warp_kernel<P><<<static_cast<unsigned>(grid), threads, 0, s>>>(r);
+    } else {
+        const int64_t grid = (r.n_i + threads - 1) / threads;
+        reduce_kernel<P><<<static_cast<unsigned>(grid), threads, 0, s>>>(r);
+    }
+    return cudaGetLastError();
+}
+
+template <class P>
+inline cudaError_t launch_batched(const BatchParams &b, int grid, int threads, cudaStream_t s) {
+    batched_kernel<P><<<grid, threads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <class P>
+inline cudaError_t occupancy_batched(int threads, int *blocks) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<P>, threads, 0);
+}
+
+}  // namespace sp2
+
+// Defines the five per-TU entry points for force policy template POLICY<ORDER, NN>.
+#define SP2_DEFINE_FORCE_TU(SUFFIX, POLICY, ORDER)                                                         \
+    namespace sp2 {                                                                                        \
+    cudaError_t launch_force_##SUFFIX(const KernelKey &k, const ForceParams &p, int grid, int threads,     \
+                                      size_t smem, cudaStream_t s) {                                       \
+        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, smem, s, nullptr)  \
+                    : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, smem, s, nullptr);\
+    }                                                                                                      \
+    cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t smem, int *blocks) {       \
+        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks)  \
+                    : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks);\
+    }                                                                                                      \
+    cudaError_t launch_reduce_##SUFFIX(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {        \
+        return k.nn ? launch_reduce<POLICY<ORDER, true>>(r, s) : launch_reduce<POLICY<ORDER, false>>(r, s); \
+    }                                                                                                      \
+    cudaError_t launch_batched_##SUFFIX(int nn, const BatchParams &b, int grid, int threads,               \
+                                        cudaStream_t s) {                                                  \
+        return nn ? launch_batched<POLICY<ORDER, true>>(b, grid, threads, s)                               \
+                  : launch_batched<POLICY<ORDER, false>>(b, grid, threads, s);                             \
+    }                                                                                                      \
+    cudaError_t occupancy_batched_##SUFFIX(int nn, int threads, int *blocks) {                             \
+        return nn ? occupancy_batched<POLICY<ORDER, true>>(threads, blocks)                                \
+                  : occupancy_batched<POLICY<ORDER, false>>(threads, blocks);                              \
+    }                                                                                                      \
+    }

@@ -1,0 +1,153 @@
+// sp2_internal.h -- declarations shared by the host API and the kernel
+// translation units of the gravity library.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sapporo_gb.h"
+
+namespace sp2 {
+
+// Device copy of the j-particles, FP64, in the caller's layout (Sec. 2.2.2:
+// particle data is always stored in double precision).
+struct JStore {
+    int32_t *id;
+    double *m, *x, *v, *a, *jk, *sn, *t;  // x/v/a/jk/sn: n x 3 row-major
+};
+
+// Bytes of one predicted record.
+//   mixed H4: {xh yh zh m}{xl yl zl id}{vx vy vz 0}            48 B
+//   mixed H6: + {ax ay az 0}                                   64 B
+//   fp64  H4: {x y}{z m}{vx vy}{vz id}                         64 B
+//   fp64  H6: + {ax ay}{az 0}                                  96 B
+//   mixed VJP: {xh yh zh m}{xl yl zl pbar}{v 0}{abar 0}{jbar 0} 80 B
+//   fp64  VJP: {x y}{z m}{vx vy}{vz pbar}{abar x y}{abar z, jbar x}{jbar y z} 112 B
+inline int record_bytes(int order, int mixed) {
+    if (mixed) return order == 6 ? 64 : 48;
+    return order == 6 ? 96 : 64;
+}
+inline int vjp_record_bytes(int mixed) { return mixed ? 80 : 112; }
+
+// Parameters of one force-kernel launch (persistent grid over work items
+// (i-block, j-slice); see sp2_device.cuh).
+struct ForceParams {
+    const unsigned char *rec;  // predicted records, slot 0
+    const int32_t *i_idx;      // sink slots (n_i)
+    int64_t n_i;
+    int64_t j_begin, j_end;    // source slots [j_begin, j_end)
+    int64_t slice_len;         // sources per slice
+    int split;                 // slices
+    int jl;                    // threads per sink
+    int tile;                  // records per shared-memory stage
+    int sinks_per_cta;         // threads / jl * ipt
+    int64_t n_iblk;            // i-blocks
+    int64_t n_items;           // n_iblk * split
+    unsigned int *queue;       // work-queue counter, zero at launch
+    unsigned int *err;         // set to 1 when a sink slot is outside [0, n_loaded)
+    int64_t n_loaded;
+    double eps2;
+    // final outputs (split == 1); any may be null
+    double *acc, *jerk, *snap, *pot;
+    int32_t *nn_id;
+    double *nn_r2;
+    // partial results (split > 1): part[f * split * n_i + slice * n_i + i]
+    double *part;
+    int32_t *part_id;          // [slice * n_i + i]
+    // VJP outputs / flags
+    double *xbar, *vbar, *mbar;
+    int accumulate;
+};
+
+struct ReduceParams {
+    const double *part;
+    const int32_t *part_id;
+    int64_t n_i;
+    int split;
+    double *acc, *jerk, *snap, *pot;
+    int32_t *nn_id;
+    double *nn_r2;
+    double *xbar, *vbar, *mbar;
+    int accumulate;
+};
+
+struct BatchParams {
+    const unsigned char *rec;
+    const int4 *items;         // {system first slot, system size, chunk first slot, chunk size}
+    int64_t n_items;
+    int64_t out_base;          // slot of output row 0
+    unsigned int *queue;
+    double eps2;
+    double *acc, *jerk, *snap, *pot;
+    int32_t *nn_id;
+    double *nn_r2;
+};
+
+enum Kind { K_FORCE = 0, K_VJP = 1 };
+
+struct KernelKey {
+    int kind;   // K_FORCE / K_VJP
+    int order;  // 4 / 6 (VJP: 4)
+    int mixed;  // 0 / 1
+    int nn;     // 0 / 1
+    int ipt;    // 1 / 2 / 4
+};
+
+// Each kernel translation unit provides these for its (order, precision).
+// They return cudaErrorInvalidValue for a key they do not hold.
+cudaError_t launch_force_kernel(const KernelKey &k, const ForceParams &p, int grid, int threads,
+                                size_t smem, cudaStream_t s);
+cudaError_t force_kernel_occupancy(const KernelKey &k, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_reduce_kernel(const KernelKey &k, const ReduceParams &p, cudaStream_t s);
+cudaError_t launch_batched_kernel(int order, int mixed, int nn, const BatchParams &p, int grid,
+                                  int threads, cudaStream_t s);
+cudaError_t batched_kernel_occupancy(int order, int mixed, int nn, int threads, int *blocks_per_sm);
+
+// Per-(order, precision) entry points, defined in sp2_kernels_*.cu.
+#define SP2_DECLARE_TU(SUFFIX)                                                                     \
+    cudaError_t launch_force_##SUFFIX(const KernelKey &, const ForceParams &, int, int, size_t,    \
+                                      cudaStream_t);                                               \
+    cudaError_t occupancy_force_##SUFFIX(const KernelKey &, int, size_t, int *);                   \
+    cudaError_t launch_reduce_##SUFFIX(const KernelKey &, const ReduceParams &, cudaStream_t);     \
+    cudaError_t launch_batched_##SUFFIX(int, const BatchParams &, int, int, cudaStream_t);         \
+    cudaError_t occupancy_batched_##SUFFIX(int, int, int *);
+SP2_DECLARE_TU(h4m)
+SP2_DECLARE_TU(h4d)
+SP2_DECLARE_TU(h6m)
+SP2_DECLARE_TU(h6d)
+SP2_DECLARE_TU(vjpm)
+SP2_DECLARE_TU(vjpd)
+#undef SP2_DECLARE_TU
+
+// Predictor and element-wise kernels (sp2_predict.cu).
+// slots outside [0, n_loaded) are skipped and set *err (device word) to 1.
+cudaError_t launch_scatter_j(const JStore &dst, const int32_t *slots, int64_t n, int64_t n_loaded,
+                             unsigned int *err, const int32_t *id, const double *m, const double *x,
+                             const double *v, const double *a, const double *jk, const double *sn,
+                             const double *t, cudaStream_t s);
+cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, double t,
+                           unsigned char *rec, cudaStream_t s);
+// (m, x, v) -> order-4 records with no prediction (all-pairs entry points)
+cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const double *x,
+                              const double *v, unsigned char *rec, cudaStream_t s);
+cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
+cudaError_t launch_h4_predict_pack(int mixed, int64_t n, double dt, const double *m,
+                                   const double *x, const double *v, const double *a,
+                                   const double *jk, unsigned char *rec, cudaStream_t s);
+cudaError_t launch_h4_correct(int64_t n, double dt, double *x, double *v, double *a, double *jk,
+                              const double *a1, const double *j1, cudaStream_t s);
+// Step VJP, part 1: output cotangents -> force cotangents + VJP records of the
+// predicted state.  Part 2: combine into input cotangents (in place).
+cudaError_t launch_h4_vjp_pre(int mixed, int64_t n, double dt, const double *m, const double *x,
+                              const double *v, const double *a, const double *jk,
+                              const double *gx, const double *gv, const double *ga,
+                              const double *gj, unsigned char *vrec, cudaStream_t s);
+cudaError_t launch_h4_vjp_post(int64_t n, double dt, const double *xpbar, const double *vpbar,
+                               double *gx, double *gv, double *ga, double *gj, cudaStream_t s);
+cudaError_t launch_pack_vjp(int mixed, int64_t n, const double *m, const double *x,
+                            const double *v, const double *abar, const double *jbar,
+                            const double *pbar, unsigned char *vrec, cudaStream_t s);
+cudaError_t launch_scan_finite(const double *p, int64_t n, unsigned int *flag, cudaStream_t s);
+
+}  // namespace sp2

@@ -1,0 +1,315 @@
+// sp2_predict.cu -- O(N) kernels around the pairwise passes: the copy
+// (scatter) kernel and the Taylor predictor of Sec. 2.2.4, the record packing
+// for the all-pairs entry points, and the element-wise parts of the shared
+// time-step Hermite-4 step and its reverse.
+//
+// The predictor is memory bound (it reads ~116-140 B and writes 48-96 B per
+// particle).  It evaluates each Taylor sum left to right with explicitly
+// rounded multiplies and adds (no fused multiply-add), dt^k/k! formed as dt^k
+// times the double nearest 1/k!, so the predicted FP64 values are those of a
+// plain IEEE evaluation of the polynomial.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sp2_internal.h"
+
+namespace sp2 {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n) { return static_cast<unsigned>((n + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+
+// Double-single split: hi = fl32(x), lo = fl32(x - hi).
+__device__ __forceinline__ void ds_split(double x, float &hi, float &lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - static_cast<double>(hi));
+}
+
+__device__ __forceinline__ void store_mixed(unsigned char *rec, int rb, int64_t j, const double *xp,
+                                            const double *vp, const double *ap, double m, int id) {
+    float xh[3], xl[3];
+    for (int c = 0; c < 3; ++c) ds_split(xp[c], xh[c], xl[c]);
+    float4 *o = reinterpret_cast<float4 *>(rec + j * rb);
+    o[0] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
+    o[1] = make_float4(xl[0], xl[1], xl[2], __int_as_float(id));
+    o[2] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]), __double2float_rn(vp[2]), 0.f);
+    if (ap) o[3] = make_float4(__double2float_rn(ap[0]), __double2float_rn(ap[1]), __double2float_rn(ap[2]), 0.f);
+}
+
+__device__ __forceinline__ void store_fp64(unsigned char *rec, int rb, int64_t j, const double *xp,
+                                           const double *vp, const double *ap, double m, int id) {
+    double2 *o = reinterpret_cast<double2 *>(rec + j * rb);
+    o[0] = make_double2(xp[0], xp[1]);
+    o[1] = make_double2(xp[2], m);
+    o[2] = make_double2(vp[0], vp[1]);
+    o[3] = make_double2(vp[2], __longlong_as_double(static_cast<long long>(id)));
+    if (ap) {
+        o[4] = make_double2(ap[0], ap[1]);
+        o[5] = make_double2(ap[2], 0.0);
+    }
+}
+
+__global__ void scatter_kernel(JStore d, const int32_t *slots, int64_t n, int64_t n_loaded, unsigned int *err,
+                               const int32_t *id, const double *m, const double *x, const double *v,
+                               const double *a, const double *jk, const double *sn, const double *t) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t s = slots[k];
+    if (s < 0 || s >= n_loaded) {  // reported by sp2_sync; the particle is not stored
+        atomicOr(err, 1u);
+        return;
+    }
+    d.id[s] = id[k];
+    d.m[s] = m[k];
+    d.t[s] = t[k];
+    for (int c = 0; c < 3; ++c) {
+        d.x[3 * s + c] = x[3 * k + c];
+        d.v[3 * s + c] = v[3 * k + c];
+        d.a[3 * s + c] = a[3 * k + c];
+        d.jk[3 * s + c] = jk[3 * k + c];
+        if (sn) d.sn[3 * s + c] = sn[3 * k + c];
+    }
+}
+
+template <int ORDER, bool MIXED>
+__global__ void predict_kernel(JStore js, int64_t n, double t, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double c2 = 0.5, c3 = 1.0 / 6.0, c4 = 1.0 / 24.0;
+    const double dt = dadd(t, -js.t[j]);
+    const double dt2 = dmul(dt, dt);
+    const double dt3 = dmul(dt2, dt);
+    const double dt4 = dmul(dt3, dt);
+    const double h2 = dmul(dt2, c2), h3 = dmul(dt3, c3), h4 = dmul(dt4, c4);
+    double xp[3], vp[3], ap[3];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = 3 * j + c;
+        const double x = js.x[q], v = js.v[q], a = js.a[q], jk = js.jk[q];
+        if (ORDER == 6) {
+            const double s = js.sn[q];
+            xp[c] = dadd(dadd(dadd(dadd(x, dmul(v, dt)), dmul(a, h2)), dmul(jk, h3)), dmul(s, h4));
+            vp[c] = dadd(dadd(dadd(v, dmul(a, dt)), dmul(jk, h2)), dmul(s, h3));
+            ap[c] = dadd(dadd(a, dmul(jk, dt)), dmul(s, h2));
+        } else {
+            xp[c] = dadd(dadd(dadd(x, dmul(v, dt)), dmul(a, h2)), dmul(jk, h3));
+            vp[c] = dadd(dadd(v, dmul(a, dt)), dmul(jk, h2));
+        }
+    }
+    const int rb = MIXED ? (ORDER == 6 ? 64 : 48) : (ORDER == 6 ? 96 : 64);
+    if (MIXED) store_mixed(rec, rb, j, xp, vp, ORDER == 6 ? ap : nullptr, js.m[j], js.id[j]);
+    else store_fp64(rec, rb, j, xp, vp, ORDER == 6 ? ap : nullptr, js.m[j], js.id[j]);
+}
+
+template <bool MIXED>
+__global__ void pack_state_kernel(int64_t n, const double *m, const double *x, const double *v, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double xp[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
+    const double vp[3] = {v[3 * j], v[3 * j + 1], v[3 * j + 2]};
+    if (MIXED) store_mixed(rec, 48, j, xp, vp, nullptr, m[j], static_cast<int>(j));
+    else store_fp64(rec, 64, j, xp, vp, nullptr, m[j], static_cast<int>(j));
+}
+
+__global__ void iota_kernel(int32_t *dst, int64_t n) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = static_cast<int32_t>(j);
+}
+
+// Hermite-4 predictor of the shared-step scheme (to t + dt), packed as records.
+template <bool MIXED>
+__global__ void h4_predict_pack_kernel(int64_t n, double dt, const double *m, const double *x, const double *v,
+                                       const double *a, const double *jk, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double h2 = dt * dt * 0.5, h3 = dt * dt * dt * (1.0 / 6.0);
+    double xp[3], vp[3];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = 3 * j + c;
+        xp[c] = x[q] + v[q] * dt + a[q] * h2 + jk[q] * h3;
+        vp[c] = v[q] + a[q] * dt + jk[q] * h2;
+    }
+    if (MIXED) store_mixed(rec, 48, j, xp, vp, nullptr, m[j], static_cast<int>(j));
+    else store_fp64(rec, 64, j, xp, vp, nullptr, m[j], static_cast<int>(j));
+}
+
+// Hermite-4 corrector (Makino & Aarseth 1992), in place; a1, j1 at the predicted state.
+__global__ void h4_correct_kernel(int64_t n3, double dt, double *x, double *v, double *a, double *jk,
+                                  const double *a1, const double *j1) {
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= n3) return;
+    const double h = 0.5 * dt, h12 = dt * dt / 12.0;
+    const double v1 = v[q] + (a[q] + a1[q]) * h + (jk[q] - j1[q]) * h12;
+    x[q] = x[q] + (v[q] + v1) * h + (a[q] - a1[q]) * h12;
+    v[q] = v1;
+    a[q] = a1[q];
+    jk[q] = j1[q];
+}
+
+__device__ __forceinline__ void store_vjp(bool mixed, unsigned char *rec, int64_t j, const double *xp, const double *vp,
+                                          const double *ab, const double *jb, double pb, double m) {
+    if (mixed) {
+        float xh[3], xl[3];
+        for (int c = 0; c < 3; ++c) ds_split(xp[c], xh[c], xl[c]);
+        float4 *o = reinterpret_cast<float4 *>(rec + j * 80);
+        o[0] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
+        o[1] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(pb));
+        o[2] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]), __double2float_rn(vp[2]), 0.f);
+        o[3] = make_float4(__double2float_rn(ab[0]), __double2float_rn(ab[1]), __double2float_rn(ab[2]), 0.f);
+        o[4] = make_float4(__double2float_rn(jb[0]), __double2float_rn(jb[1]), __double2float_rn(jb[2]), 0.f);
+    } else {
+        double2 *o = reinterpret_cast<double2 *>(rec + j * 112);
+        o[0] = make_double2(xp[0], xp[1]);
+        o[1] = make_double2(xp[2], m);
+        o[2] = make_double2(vp[0], vp[1]);
+        o[3] = make_double2(vp[2], pb);
+        o[4] = make_double2(ab[0], ab[1]);
+        o[5] = make_double2(ab[2], jb[0]);
+        o[6] = make_double2(jb[1], jb[2]);
+    }
+}
+
+template <bool MIXED>
+__global__ void pack_vjp_kernel(int64_t n, const double *m, const double *x, const double *v, const double *abar,
+                                const double *jbar, const double *pbar, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double zero[3] = {0.0, 0.0, 0.0};
+    const double *ab = abar ? abar + 3 * j : zero;
+    const double *jb = jbar ? jbar + 3 * j : zero;
+    store_vjp(MIXED, rec, j, x + 3 * j, v + 3 * j, ab, jb, pbar ? pbar[j] : 0.0, m[j]);
+}
+
+// Reverse of the corrector for the output cotangents (gx, gv, ga, gj):
+//   gv1 = gv + gx dt/2,  ga1 = ga + gv1 dt/2 - gx dt^2/12,  gj1 = gj - gv1 dt^2/12
+// are the cotangents of the force outputs (a1, j1) at the predicted state,
+// which is recomputed here and packed with them into VJP records.
+template <bool MIXED>
+__global__ void h4_vjp_pre_kernel(int64_t n, double dt, const double *m, const double *x, const double *v,
+                                  const double *a, const double *jk, const double *gx, const double *gv,
+                                  const double *ga, const double *gj, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double h2 = dt * dt * 0.5, h3 = dt * dt * dt * (1.0 / 6.0), h12 = dt * dt / 12.0;
+    double xp[3], vp[3], ab[3], jb[3];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = 3 * j + c;
+        xp[c] = x[q] + v[q] * dt + a[q] * h2 + jk[q] * h3;
+        vp[c] = v[q] + a[q] * dt + jk[q] * h2;
+        const double gv1 = gv[q] + gx[q] * (0.5 * dt);
+        ab[c] = ga[q] + gv1 * (0.5 * dt) - gx[q] * h12;
+        jb[c] = gj[q] - gv1 * h12;
+    }
+    store_vjp(MIXED, rec, j, xp, vp, ab, jb, 0.0, m[j]);
+}
+
+// Combine: cotangents of the step inputs from the output cotangents and the
+// force VJP (xpbar, vpbar) at the predicted state.
+__global__ void h4_vjp_post_kernel(int64_t n3, double dt, const double *xpbar, const double *vpbar, double *gx,
+                                   double *gv, double *ga, double *gj) {
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= n3) return;
+    const double h = 0.5 * dt, h2 = dt * dt * 0.5, h3 = dt * dt * dt * (1.0 / 6.0), h12 = dt * dt / 12.0;
+    const double gx1 = gx[q];
+    const double gv1 = gv[q] + gx1 * h;
+    const double xb = xpbar[q], vb = vpbar[q];
+    gx[q] = gx1 + xb;
+    gv[q] = gx1 * h + gv1 + xb * dt + vb;
+    ga[q] = gx1 * h12 + gv1 * h + xb * h2 + vb * dt;
+    gj[q] = gv1 * h12 + xb * h3 + vb * h2;
+}
+
+__global__ void scan_finite_kernel(const double *p, int64_t n, unsigned int *flag) {
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q < n && !isfinite(p[q])) atomicOr(flag, 1u);
+}
+
+}  // namespace
+
+cudaError_t launch_scatter_j(const JStore &dst, const int32_t *slots, int64_t n, int64_t n_loaded, unsigned int *err,
+                             const int32_t *id, const double *m, const double *x, const double *v, const double *a,
+                             const double *jk, const double *sn, const double *t, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    scatter_kernel<<<grid_for(n), kThreads, 0, s>>>(dst, slots, n, n_loaded, err, id, m, x, v, a, jk, sn, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, double t, unsigned char *rec,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned g = grid_for(n);
+    if (order == 6) {
+        if (mixed) predict_kernel<6, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
+        else predict_kernel<6, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
+    } else {
+        if (mixed) predict_kernel<4, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
+        else predict_kernel<4, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const double *x, const double *v,
+                              unsigned char *rec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (mixed) pack_state_kernel<true><<<grid_for(n), kThreads, 0, s>>>(n, m, x, v, rec);
+    else pack_state_kernel<false><<<grid_for(n), kThreads, 0, s>>>(n, m, x, v, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    iota_kernel<<<grid_for(n), kThreads, 0, s>>>(dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h4_predict_pack(int mixed, int64_t n, double dt, const double *m, const double *x,
+                                   const double *v, const double *a, const double *jk, unsigned char *rec,
+                                   cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (mixed) h4_predict_pack_kernel<true><<<grid_for(n), kThreads, 0, s>>>(n, dt, m, x, v, a, jk, rec);
+    else h4_predict_pack_kernel<false><<<grid_for(n), kThreads, 0, s>>>(n, dt, m, x, v, a, jk, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h4_correct(int64_t n, double dt, double *x, double *v, double *a, double *jk, const double *a1,
+                              const double *j1, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    h4_correct_kernel<<<grid_for(3 * n), kThreads, 0, s>>>(3 * n, dt, x, v, a, jk, a1, j1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h4_vjp_pre(int mixed, int64_t n, double dt, const double *m, const double *x, const double *v,
+                              const double *a, const double *jk, const double *gx, const double *gv,
+                              const double *ga, const double *gj, unsigned char *vrec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (mixed) h4_vjp_pre_kernel<true><<<grid_for(n), kThreads, 0, s>>>(n, dt, m, x, v, a, jk, gx, gv, ga, gj, vrec);
+    else h4_vjp_pre_kernel<false><<<grid_for(n), kThreads, 0, s>>>(n, dt, m, x, v, a, jk, gx, gv, ga, gj, vrec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h4_vjp_post(int64_t n, double dt, const double *xpbar, const double *vpbar, double *gx,
+                               double *gv, double *ga, double *gj, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    h4_vjp_post_kernel<<<grid_for(3 * n), kThreads, 0, s>>>(3 * n, dt, xpbar, vpbar, gx, gv, ga, gj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_vjp(int mixed, int64_t n, const double *m, const double *x, const double *v,
+                            const double *abar, const double *jbar, const double *pbar, unsigned char *vrec,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (mixed) pack_vjp_kernel<true><<<grid_for(n), kThreads, 0, s>>>(n, m, x, v, abar, jbar, pbar, vrec);
+    else pack_vjp_kernel<false><<<grid_for(n), kThreads, 0, s>>>(n, m, x, v, abar, jbar, pbar, vrec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_finite(const double *p, int64_t n, unsigned int *flag, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    scan_finite_kernel<<<grid_for(n), kThreads, 0, s>>>(p, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace sp2
