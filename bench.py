@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--launch", default=None,
+                   help="force the force-kernel launch shape: threads,i_per_thread,j_lanes,j_tile,split_j")
     return p.parse_args()
 
 
@@ -151,6 +153,41 @@ def peaks():
         return {}
 
 
+FORCE_SOURCES = ("paper_1510_04068_gb300/csrc/sp2_device.cuh", "paper_1510_04068_gb300/csrc/sp2_kernels_h4m.cu")
+TRAFFIC_SUMMARY = "profiles/force_h4_mixed_131072.md"
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in FORCE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes of one full-size (N = N_active = 131072) force launch from the
+    committed ncu summary, or None when the kernel source changed since the
+    counters were taken."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_SUMMARY)) as fh:
+            txt = fh.read()
+    except OSError:
+        return None, None
+    vals = {}
+    for ln in txt.splitlines():
+        if "=" in ln and ln.strip().startswith("- `"):
+            k, _, v = ln.strip()[3:].partition("=")
+            vals[k.strip(" `")] = v.strip(" `")
+    if vals.get("source_sha256_16") != kernel_source_hash():
+        return None, vals.get("source_sha256_16")
+    try:
+        return float(vals["dram_bytes_per_launch_131072"]), vals.get("source_sha256_16")
+    except (KeyError, ValueError):
+        return None, None
+
+
 def make_workload(n, n_active, seed=0):
     m, x, v = W.plummer(n, seed)
     a, jk, _ = W.derivative_noise(n, seed + 1, scales=(1.0, 4.0, 16.0))
@@ -239,7 +276,13 @@ def run_ours(args, world, rank, local):
                           cuda_stream=stream.cuda_stream)
         ctx.set_j(0, full["ids"], full["m"], full["x"], full["v"], full["a"], full["jerk"], None, full["tj"])
         ctx.predict(w["t"])
-        tuned = None if args.no_tune else ctx.autotune(n_act)
+        if args.launch:
+            th, ipt, jl, tile, split = (int(q) for q in args.launch.split(","))
+            ctx.set_launch(n_act, dict(threads=th, i_per_thread=ipt, j_lanes=jl, j_tile=tile, split_j=split,
+                                       ctas_per_sm=0))
+            tuned = None
+        else:
+            tuned = None if args.no_tune else ctx.autotune(n_act)
         launch = ctx.get_launch(n_act)
 
         def step(k):
@@ -282,6 +325,8 @@ def run_ours(args, world, rank, local):
     peak_tops = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
     achieved = inter_step * OPS_PER_INTERACTION / (force_ms / 1e3) / 1e12
     clocks = clk.summary()
+    tb, _sha = committed_traffic()
+    traffic = tb if (tb is not None and n == 131072 and n_act == 131072) else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -294,7 +339,8 @@ def run_ours(args, world, rank, local):
                    "wall_ms_incl_flush": 1e3 * (wall1 - wall0) / args.steps},
         "stages_ms_per_step": {k: (v[1] / args.steps) for k, v in prof.items() if v[0]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (FP32 lane-instr)",
-                     "frac": achieved / peak_tops, "traffic": None,
+                     "frac": achieved / peak_tops, "traffic": traffic,
+                     "traffic_source": TRAFFIC_SUMMARY if traffic is not None else None,
                      "kernel": "pass_kernel<MixedForce<4,NN>>", "force_ms_per_launch": force_ms,
                      "ops_per_interaction": OPS_PER_INTERACTION,
                      "peak_basis": f"{dev_props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "

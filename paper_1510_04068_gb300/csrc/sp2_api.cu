@@ -184,8 +184,8 @@ sp2_status check_launch(sp2_ctx *c, const sp2_launch &L) {
         return fail(c, SP2_ERR_ARG, "i_per_thread must be 1, 2 or 4");
     if (!pow2(L.j_lanes) || L.j_lanes > 32 || L.j_lanes > L.threads)
         return fail(c, SP2_ERR_ARG, "j_lanes must be a power of two <= min(32, threads)");
-    if (L.j_tile < 16 || L.j_tile > 1024 || L.j_tile % L.j_lanes != 0 || L.j_tile % 16 != 0)
-        return fail(c, SP2_ERR_ARG, "j_tile must be a multiple of 16 and of j_lanes, in [16, 1024]");
+    if (L.j_tile < 16 || L.j_tile > 1024 || !pow2(L.j_tile) || L.j_tile < 8 * L.j_lanes)
+        return fail(c, SP2_ERR_ARG, "j_tile must be a power of two in [16, 1024] and >= 8 * j_lanes");
     if (L.split_j < 1 || L.split_j > 65536) return fail(c, SP2_ERR_ARG, "split_j must be in [1, 65536]");
     if (L.ctas_per_sm < 0 || L.ctas_per_sm > 32) return fail(c, SP2_ERR_ARG, "ctas_per_sm must be in [0, 32]");
     return SP2_OK;
@@ -209,6 +209,7 @@ sp2_launch heuristic(const sp2_ctx *c, int kind, int mixed, int64_t n_i, int64_t
     while (L.threads > 32 && L.threads / 2 >= L.j_lanes &&
            static_cast<int64_t>(L.threads / 2 / L.j_lanes) * L.i_per_thread >= n_i)
         L.threads /= 2;
+    L.j_tile = std::max(L.j_tile, 8 * L.j_lanes);
     const int64_t sinks_per_cta = static_cast<int64_t>(L.threads / L.j_lanes) * L.i_per_thread;
     const int64_t n_iblk = ceil_div(n_i, sinks_per_cta);
     const int64_t cta_slots = static_cast<int64_t>(c->sm_count) * std::max(1, 512 / L.threads);
@@ -229,9 +230,10 @@ struct PassOut {
     int accumulate = 0;
 };
 
+// rec holds n_valid records; sink slots must lie in [0, n_valid).
 sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const unsigned char *rec, int rb,
-                    const int32_t *i_idx, int64_t n_i, int64_t j_begin, int64_t j_end, const PassOut &o,
-                    const sp2_launch *forced, int stage_force, float *ms_out = nullptr) {
+                    int64_t n_valid, const int32_t *i_idx, int64_t n_i, int64_t j_begin, int64_t j_end,
+                    const PassOut &o, const sp2_launch *forced, int stage_force, float *ms_out = nullptr) {
     if (n_i <= 0) return SP2_OK;
     sp2_launch L;
     if (forced) {
@@ -250,7 +252,11 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
     const size_t smem = static_cast<size_t>(kStagesDevice) * tile * rb;
-    if (smem > 160 * 1024) return fail(c, SP2_ERR_ARG, "j_tile %d needs %zu bytes of shared memory (max 160 KiB)", tile, smem);
+    const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
+    const size_t smem_total = smem + (mixed ? static_cast<size_t>(L.threads) * L.i_per_thread * ns_fields * 8 : 0);
+    if (smem_total > 200 * 1024)
+        return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max 200 KiB)", smem_total);
+    if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
     int per_sm = L.ctas_per_sm;
     if (per_sm <= 0) {
         SP2_CK(c, force_kernel_occupancy(key, L.threads, smem, &per_sm));
@@ -274,11 +280,11 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     p.n_items = n_items;
     p.queue = c->dev_words;
     p.err = c->dev_words + 1;
-    p.n_loaded = c->n_loaded;
+    p.n_loaded = n_valid;
     p.eps2 = c->cfg.eps2;
     p.acc = o.acc; p.jerk = o.jerk; p.snap = o.snap; p.pot = o.pot; p.nn_id = o.nn_id; p.nn_r2 = o.nn_r2;
     p.xbar = o.xbar; p.vbar = o.vbar; p.mbar = o.mbar; p.accumulate = o.accumulate;
-    const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
+    const int ns = ns_fields;
     if (split > 1) {
         const size_t need = static_cast<size_t>(ns + (nn ? 1 : 0)) * split * n_i * sizeof(double);
         SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->part), &c->part_cap, need, "partial-sum"));
@@ -665,7 +671,7 @@ sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t
         o.acc = acc; o.jerk = jerk; o.snap = snap; o.pot = pot; o.nn_id = nn_id; o.nn_r2 = nn_r2;
     }
     const int nn = c->cfg.with_nn && (o.nn_id || o.nn_r2);
-    SP2_CKS(run_pass(c, K_FORCE, c->cfg.order, mixed, nn, c->rec, c->rb, d_idx, n_i, j_begin, j_end, o, nullptr, ST_FORCE));
+    SP2_CKS(run_pass(c, K_FORCE, c->cfg.order, mixed, nn, c->rec, c->rb, c->n_loaded, d_idx, n_i, j_begin, j_end, o, nullptr, ST_FORCE));
     const double *arrs[4] = {o.acc, o.jerk, o.snap, o.pot};
     const int64_t lens[4] = {3 * n_i, 3 * n_i, 3 * n_i, n_i};
     SP2_CKS(finite_check(c, arrs, lens, 4));
@@ -808,7 +814,7 @@ sp2_status sp2_forces(sp2_ctx *c, int64_t n, const double *m, const double *x, c
     }
     SP2_CK(c, launch_pack_state(mixed, n, m, x, v, c->rec2, c->stream));
     c->launches += 1;
-    SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec2, record_bytes(4, mixed), c->iota, n, 0, n, o, nullptr, ST_FORCE));
+    SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec2, record_bytes(4, mixed), n, c->iota, n, 0, n, o, nullptr, ST_FORCE));
     if (ptr_kind == SP2_HOST) SP2_CKS(stage_copy_out(s));
     return SP2_OK;
 }
@@ -846,7 +852,7 @@ sp2_status sp2_force_vjp(sp2_ctx *c, int64_t n, const double *m, const double *x
     }
     SP2_CK(c, launch_pack_vjp(mixed, n, m, x, v, abar, jbar, pbar, c->rec2, c->stream));
     c->launches += 1;
-    SP2_CKS(run_pass(c, K_VJP, 4, mixed, 0, c->rec2, vjp_record_bytes(mixed), c->iota, n, 0, n, o, nullptr, ST_VJP));
+    SP2_CKS(run_pass(c, K_VJP, 4, mixed, 0, c->rec2, vjp_record_bytes(mixed), n, c->iota, n, 0, n, o, nullptr, ST_VJP));
     if (ptr_kind == SP2_HOST) SP2_CKS(stage_copy_out(s));
     return SP2_OK;
 }
@@ -864,7 +870,7 @@ sp2_status sp2_hermite4_step(sp2_ctx *c, int64_t n, double dt, const double *m, 
     PassOut o;
     o.acc = a1;
     o.jerk = j1;
-    SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec2, record_bytes(4, mixed), c->iota, n, 0, n, o, nullptr, ST_FORCE));
+    SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec2, record_bytes(4, mixed), n, c->iota, n, 0, n, o, nullptr, ST_FORCE));
     SP2_CK(c, launch_h4_correct(n, dt, x, v, a, jerk, a1, j1, c->stream));
     c->launches += 1;
     return SP2_OK;
@@ -888,7 +894,7 @@ sp2_status sp2_hermite4_step_vjp(sp2_ctx *c, int64_t n, double dt, const double 
     SP2_CK(c, cudaMemsetAsync(xpbar, 0, 3 * n * sizeof(double), c->stream));
     SP2_CK(c, cudaMemsetAsync(vpbar, 0, 3 * n * sizeof(double), c->stream));
     o.accumulate = 1;
-    SP2_CKS(run_pass(c, K_VJP, 4, mixed, 0, c->rec2, vjp_record_bytes(mixed), c->iota, n, 0, n, o, nullptr, ST_VJP));
+    SP2_CKS(run_pass(c, K_VJP, 4, mixed, 0, c->rec2, vjp_record_bytes(mixed), n, c->iota, n, 0, n, o, nullptr, ST_VJP));
     SP2_CK(c, launch_h4_vjp_post(n, dt, xpbar, vpbar, gx, gv, ga, gj, c->stream));
     c->launches += 1;
     return SP2_OK;
@@ -940,7 +946,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         cand.push_back(L);
     };
     const int ipts[3] = {1, 2, 4};
-    const int tiles[3] = {64, 128, 256};
+    const int tiles[4] = {64, 128, 256, 512};
     for (int threads : {64, 128, 256})
         for (int ipt : ipts)
             for (int jl = 1; jl <= 32; jl *= 2) {
@@ -951,7 +957,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
                 if (n_iblk * threads < int64_t(c->sm_count) * 32 && jl < 32 && threads * ipt / jl < n_i) continue;
                 if (jl > 1 && n_i * jl / ipt > int64_t(c->sm_count) * 4096) continue;
                 for (int tile : tiles) {
-                    if (tile % jl || tile / jl < 2) continue;
+                    if (tile < 8 * jl) continue;
                     const int64_t slots = int64_t(c->sm_count) * std::max(1, 512 / threads);
                     for (int mult : {1, 2, 4, 8}) {
                         sp2_launch L{threads, ipt, jl, tile, 1, 0};
@@ -977,10 +983,10 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     }
     for (size_t k = 0; k < cand.size(); ++k) {
         float ms = 0.f;
-        sp2_status s = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->iota, n_i, 0, n_j, o, &cand[k], ST_FORCE, &ms);
+        sp2_status s = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j, o, &cand[k], ST_FORCE, &ms);
         if (s == SP2_ERR_UNSUPPORTED) continue;
         if (s != SP2_OK) return s;
-        s = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->iota, n_i, 0, n_j, o, &cand[k], ST_FORCE, &ms);
+        s = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j, o, &cand[k], ST_FORCE, &ms);
         if (s != SP2_OK) return s;
         t1.push_back({ms, k});
     }
@@ -992,7 +998,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         float sum = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             float ms = 0.f;
-            SP2_CKS(run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->iota, n_i, 0, n_j, o, &cand[t1[r].second], ST_FORCE, &ms));
+            SP2_CKS(run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j, o, &cand[t1[r].second], ST_FORCE, &ms));
             sum += ms;
         }
         if (sum < best_ms) {

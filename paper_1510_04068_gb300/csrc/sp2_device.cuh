@@ -57,8 +57,12 @@ __device__ __forceinline__ void nn_merge(double &d, int &id, double od, int oid)
 // ---------------------------------------------------------------------------
 // Mixed precision force policy: positions as double-single (hi + lo FP32),
 // x_j - x_i formed as (hi_j - hi_i) + (lo_j - lo_i); rsqrt (SFU) and all terms
-// in FP32; per-thread FP32 partial sums flushed into FP64 totals every kFlush
-// sources.
+// in FP32.  Sums are kept in two FP32 levels -- a partial over kChunk sources,
+// folded into a second FP32 level -- and the second level is added into FP64
+// totals (held in shared memory, one slot per thread and sink) every kFlush
+// sources.  Sequential FP32 summation rounds every add at the scale of the
+// running sum, so a long FP32 sum dominated by one large term loses ~sqrt(k)
+// ulps; the two short levels bound that error by ~(kChunk + kFlush/kChunk) ulps.
 // ---------------------------------------------------------------------------
 template <int ORDER, bool NN>
 struct MixedForce {
@@ -66,6 +70,8 @@ struct MixedForce {
     static constexpr int RB = NW * 16;
     static constexpr int NS = (ORDER == 6) ? 10 : 7;  // summed fields
     static constexpr bool kNN = NN;
+    static constexpr bool kSmemTotals = true;
+    static constexpr int kChunk = 8;
     static constexpr int kFlush = 64;
     typedef float real;
     struct Rec {
@@ -76,10 +82,11 @@ struct MixedForce {
         int slot;
     };
     struct Acc {
-        float ax, ay, az, jx, jy, jz, sx, sy, sz, pot;
-        double Ax, Ay, Az, Jx, Jy, Jz, Sx, Sy, Sz, Pot;
-        float nn_d2;
-        int nn_j;
+        float f[NS];     // level 1: current chunk
+        float g[NS];     // level 2: chunks since the last FP64 flush
+        unsigned ck;     // nearest-neighbour key of the current chunk
+        unsigned bk;     // best key so far, and the slot of its chunk's first source
+        int bbase;
     };
 
     __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
@@ -110,13 +117,25 @@ struct MixedForce {
         else { s.ax = s.ay = s.az = 0.f; }
     }
     __device__ static __forceinline__ void init(Acc &c) {
-        c.ax = c.ay = c.az = c.jx = c.jy = c.jz = c.sx = c.sy = c.sz = c.pot = 0.f;
-        c.Ax = c.Ay = c.Az = c.Jx = c.Jy = c.Jz = c.Sx = c.Sy = c.Sz = c.Pot = 0.0;
-        c.nn_d2 = f_inf();
-        c.nn_j = -1;
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = 0.f;
+        c.ck = c.bk = 0xffffffffu;
+        c.bbase = -1;
     }
+    // Squared distance between a record and the sink, exactly as interact() forms it.
+    __device__ static __forceinline__ float dist2(const Rec &r, const Sink &s) {
+        const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
+        const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
+        const float dz = (r.w[0].z - s.zh) + (r.w[1].z - s.zl);
+        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    }
+    // fields: 0-2 acc, 3-5 jerk, [6-8 snap], NS-1 potential (accumulated as +m/r).
+    // Nearest neighbour: r^2 >= 0, so its bit pattern orders like the value;
+    // the low 3 mantissa bits carry the source's position u in the chunk (a
+    // 2^-20 relative truncation, far inside the 1e-5 tie band) and one unsigned
+    // min per interaction keeps the chunk's best.
     template <bool SELF>
-    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, float eps2) {
+    __device__ static __forceinline__ void interact(const Rec &r, int j, int u, const Sink &s, Acc &c, float eps2) {
         const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
         const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
         const float dz = (r.w[0].z - s.zh) + (r.w[1].z - s.zl);
@@ -127,16 +146,16 @@ struct MixedForce {
         const float rinv2 = rinv * rinv;
         const float mr = r.w[0].w * rinv;
         const float mr3 = mr * rinv2;
-        c.pot += mr;
+        c.f[NS - 1] += mr;
         const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
         const float al3 = 3.f * (rv * rinv2);
         if (ORDER == 4) {
-            c.ax = fmaf(mr3, dx, c.ax);
-            c.ay = fmaf(mr3, dy, c.ay);
-            c.az = fmaf(mr3, dz, c.az);
-            c.jx = fmaf(mr3, fmaf(-al3, dx, dvx), c.jx);
-            c.jy = fmaf(mr3, fmaf(-al3, dy, dvy), c.jy);
-            c.jz = fmaf(mr3, fmaf(-al3, dz, dvz), c.jz);
+            c.f[0] = fmaf(mr3, dx, c.f[0]);
+            c.f[1] = fmaf(mr3, dy, c.f[1]);
+            c.f[2] = fmaf(mr3, dz, c.f[2]);
+            c.f[3] = fmaf(mr3, fmaf(-al3, dx, dvx), c.f[3]);
+            c.f[4] = fmaf(mr3, fmaf(-al3, dy, dvy), c.f[4]);
+            c.f[5] = fmaf(mr3, fmaf(-al3, dz, dvz), c.f[5]);
         } else {
             const float dax = r.w[3].x - s.ax, day = r.w[3].y - s.ay, daz = r.w[3].z - s.az;
             const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
@@ -148,37 +167,50 @@ struct MixedForce {
             const float al = rv * rinv2;
             const float b3 = 3.f * fmaf(vv + ra, rinv2, al * al);
             const float a6 = 2.f * al3;
-            c.ax += Ax; c.ay += Ay; c.az += Az;
-            c.jx += Jx; c.jy += Jy; c.jz += Jz;
-            c.sx += fmaf(mr3, dax, -fmaf(a6, Jx, b3 * Ax));
-            c.sy += fmaf(mr3, day, -fmaf(a6, Jy, b3 * Ay));
-            c.sz += fmaf(mr3, daz, -fmaf(a6, Jz, b3 * Az));
+            c.f[0] += Ax; c.f[1] += Ay; c.f[2] += Az;
+            c.f[3] += Jx; c.f[4] += Jy; c.f[5] += Jz;
+            c.f[6] += fmaf(mr3, dax, -fmaf(a6, Jx, b3 * Ax));
+            c.f[7] += fmaf(mr3, day, -fmaf(a6, Jy, b3 * Ay));
+            c.f[8] += fmaf(mr3, daz, -fmaf(a6, Jz, b3 * Az));
         }
         if (NN) {
-            const float dn = (SELF && j == s.slot) ? f_inf() : d2;
-            if (dn < c.nn_d2) { c.nn_d2 = dn; c.nn_j = j; }
+            const unsigned key = (SELF && j == s.slot) ? 0xffffffffu : ((__float_as_uint(d2) & ~7u) | unsigned(u));
+            c.ck = min(c.ck, key);
         }
     }
-    __device__ static __forceinline__ void flush(Acc &c) {
-        c.Ax += c.ax; c.Ay += c.ay; c.Az += c.az;
-        c.Jx += c.jx; c.Jy += c.jy; c.Jz += c.jz;
-        if (ORDER == 6) { c.Sx += c.sx; c.Sy += c.sy; c.Sz += c.sz; }
-        c.Pot += c.pot;
-        c.ax = c.ay = c.az = c.jx = c.jy = c.jz = c.sx = c.sy = c.sz = c.pot = 0.f;
+    // end of a chunk whose first source (for this thread) is slot `base`
+    __device__ static __forceinline__ void fold(Acc &c, int base) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) { c.g[f] += c.f[f]; c.f[f] = 0.f; }
+        if (NN) {
+            if (c.ck < c.bk) { c.bk = c.ck; c.bbase = base; }
+            c.ck = 0xffffffffu;
+        }
     }
-    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
-        t[0] = c.Ax; t[1] = c.Ay; t[2] = c.Az;
-        t[3] = c.Jx; t[4] = c.Jy; t[5] = c.Jz;
-        if (ORDER == 6) { t[6] = c.Sx; t[7] = c.Sy; t[8] = c.Sz; t[9] = -c.Pot; }
-        else { t[6] = -c.Pot; }
+    // level 2 -> FP64 totals tot[f * stride]
+    __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) { tot[f * stride] += static_cast<double>(c.g[f]); c.g[f] = 0.f; }
     }
+    __device__ static __forceinline__ void zero_totals(double *tot, int stride) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) tot[f * stride] = 0.0;
+    }
+    __device__ static __forceinline__ void totals(const Acc &, const double *tot, int stride, double *t) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) t[f] = tot[f * stride];
+        t[NS - 1] = -t[NS - 1];
+    }
+    // The chosen source is slot bbase + u * jl; its r^2 is recomputed exactly.
     // limit: one past the last real source slot (filler records never qualify,
-    // the bound keeps the id lookup inside the record array regardless).
-    __device__ static __forceinline__ void nn(const Acc &c, const unsigned char *rec, int64_t limit, double &d,
-                                              int &id) {
-        if (NN && c.nn_j >= 0 && c.nn_j < limit) {
-            d = static_cast<double>(c.nn_d2);
-            id = __ldg(reinterpret_cast<const int *>(rec + static_cast<int64_t>(c.nn_j) * RB + 28));
+    // the bound keeps the lookup inside the record array regardless).
+    __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
+                                              int jl, double &d, int &id) {
+        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & 7u) * jl : -1;
+        if (NN && j >= 0 && j < limit && (c.bk & ~7u) < 0x7f800000u) {
+            const Rec r = ld_global(rec + j * RB);
+            d = static_cast<double>(dist2(r, s));
+            id = __float_as_int(r.w[1].w);
         } else {
             d = d_inf();
             id = -1;
@@ -208,6 +240,8 @@ struct Fp64Force {
     static constexpr int RB = NW * 16;
     static constexpr int NS = (ORDER == 6) ? 10 : 7;
     static constexpr bool kNN = NN;
+    static constexpr bool kSmemTotals = false;
+    static constexpr int kChunk = 8;
     static constexpr int kFlush = 1 << 30;
     typedef double real;
     struct Rec {
@@ -253,7 +287,7 @@ struct Fp64Force {
         c.nn_id = -1;
     }
     template <bool SELF>
-    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, double eps2) {
+    __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, double eps2) {
         const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
         const double m = r.w[1].y;
         const double dvx = r.w[2].x - s.vx, dvy = r.w[2].y - s.vy, dvz = r.w[3].x - s.vz;
@@ -290,14 +324,17 @@ struct Fp64Force {
             }
         }
     }
-    __device__ static __forceinline__ void flush(Acc &) {}
-    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
+    __device__ static __forceinline__ void fold(Acc &, int) {}
+    __device__ static __forceinline__ void flush(Acc &, double *, int) {}
+    __device__ static __forceinline__ void zero_totals(double *, int) {}
+    __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
         t[0] = c.ax; t[1] = c.ay; t[2] = c.az;
         t[3] = c.jx; t[4] = c.jy; t[5] = c.jz;
         if (ORDER == 6) { t[6] = c.sx; t[7] = c.sy; t[8] = c.sz; t[9] = c.pot; }
         else { t[6] = c.pot; }
     }
-    __device__ static __forceinline__ void nn(const Acc &c, const unsigned char *, int64_t, double &d, int &id) {
+    __device__ static __forceinline__ void nn(const Acc &c, const Sink &, const unsigned char *, int64_t, int, double &d,
+                                              int &id) {
         d = c.nn_d2;
         id = NN ? c.nn_id : -1;
         if (id < 0) d = d_inf();
@@ -326,6 +363,8 @@ struct MixedVjp {
     static constexpr int RB = 80;
     static constexpr int NS = 7;
     static constexpr bool kNN = false;
+    static constexpr bool kSmemTotals = true;
+    static constexpr int kChunk = 8;
     static constexpr int kFlush = 64;
     typedef float real;
     struct Rec {
@@ -336,8 +375,8 @@ struct MixedVjp {
         int slot;
     };
     struct Acc {
-        float gx, gy, gz, hx, hy, hz, gm;
-        double Gx, Gy, Gz, Hx, Hy, Hz, Gm;
+        float f[NS];  // level 1: xbar (3), vbar (3), mbar over the current chunk
+        float g[NS];  // level 2
     };
     __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
         Rec r;
@@ -364,11 +403,11 @@ struct MixedVjp {
         s.jbx = r.w[4].x; s.jby = r.w[4].y; s.jbz = r.w[4].z;
     }
     __device__ static __forceinline__ void init(Acc &c) {
-        c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.f;
-        c.Gx = c.Gy = c.Gz = c.Hx = c.Hy = c.Hz = c.Gm = 0.0;
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = 0.f;
     }
     template <bool SELF>
-    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, float eps2) {
+    __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, float eps2) {
         const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
         const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
         const float dz = (r.w[0].z - s.zh) + (r.w[1].z - s.zl);
@@ -391,24 +430,32 @@ struct MixedVjp {
         const float cv = 3.f * s2 * D;
         const float cr = 3.f * s2 * (q1 * B1 - q2 * B2) - 6.f * al * s2 * D - s3 * fmaf(s.pb, ml, pl * s.m);
         const float t1 = 3.f * al * q1, t2 = 3.f * al * q2;
-        c.gx += q2 * abx - q1 * s.abx + t1 * s.jbx - t2 * jbx + cv * vx + cr * dx;
-        c.gy += q2 * aby - q1 * s.aby + t1 * s.jby - t2 * jby + cv * vy + cr * dy;
-        c.gz += q2 * abz - q1 * s.abz + t1 * s.jbz - t2 * jbz + cv * vz + cr * dz;
-        c.hx += q2 * jbx - q1 * s.jbx + cv * dx;
-        c.hy += q2 * jby - q1 * s.jby + cv * dy;
-        c.hz += q2 * jbz - q1 * s.jbz + cv * dz;
-        c.gm -= fmaf(s3, B2, pl * rinv);
+        c.f[0] += q2 * abx - q1 * s.abx + t1 * s.jbx - t2 * jbx + cv * vx + cr * dx;
+        c.f[1] += q2 * aby - q1 * s.aby + t1 * s.jby - t2 * jby + cv * vy + cr * dy;
+        c.f[2] += q2 * abz - q1 * s.abz + t1 * s.jbz - t2 * jbz + cv * vz + cr * dz;
+        c.f[3] += q2 * jbx - q1 * s.jbx + cv * dx;
+        c.f[4] += q2 * jby - q1 * s.jby + cv * dy;
+        c.f[5] += q2 * jbz - q1 * s.jbz + cv * dz;
+        c.f[6] -= fmaf(s3, B2, pl * rinv);
     }
-    __device__ static __forceinline__ void flush(Acc &c) {
-        c.Gx += c.gx; c.Gy += c.gy; c.Gz += c.gz;
-        c.Hx += c.hx; c.Hy += c.hy; c.Hz += c.hz;
-        c.Gm += c.gm;
-        c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.f;
+    __device__ static __forceinline__ void fold(Acc &c, int) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) { c.g[f] += c.f[f]; c.f[f] = 0.f; }
     }
-    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
-        t[0] = c.Gx; t[1] = c.Gy; t[2] = c.Gz; t[3] = c.Hx; t[4] = c.Hy; t[5] = c.Hz; t[6] = c.Gm;
+    __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) { tot[f * stride] += static_cast<double>(c.g[f]); c.g[f] = 0.f; }
     }
-    __device__ static __forceinline__ void nn(const Acc &, const unsigned char *, int64_t, double &d, int &id) {
+    __device__ static __forceinline__ void zero_totals(double *tot, int stride) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) tot[f * stride] = 0.0;
+    }
+    __device__ static __forceinline__ void totals(const Acc &, const double *tot, int stride, double *t) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) t[f] = tot[f * stride];
+    }
+    __device__ static __forceinline__ void nn(const Acc &, const Sink &, const unsigned char *, int64_t, int, double &d,
+                                              int &id) {
         d = d_inf();
         id = -1;
     }
@@ -431,6 +478,8 @@ struct Fp64Vjp {
     static constexpr int RB = 112;
     static constexpr int NS = 7;
     static constexpr bool kNN = false;
+    static constexpr bool kSmemTotals = false;
+    static constexpr int kChunk = 8;
     static constexpr int kFlush = 1 << 30;
     typedef double real;
     struct Rec {
@@ -469,7 +518,7 @@ struct Fp64Vjp {
     }
     __device__ static __forceinline__ void init(Acc &c) { c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.0; }
     template <bool SELF>
-    __device__ static __forceinline__ void interact(const Rec &r, int j, const Sink &s, Acc &c, double eps2) {
+    __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, double eps2) {
         const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
         const double vx = r.w[2].x - s.vx, vy = r.w[2].y - s.vy, vz = r.w[3].x - s.vz;
         const double d2 = dx * dx + dy * dy + dz * dz;
@@ -497,11 +546,14 @@ struct Fp64Vjp {
         c.hz += q2 * jbz - q1 * s.jbz + cv * dz;
         c.gm -= s3 * B2 + pl * rinv;
     }
-    __device__ static __forceinline__ void flush(Acc &) {}
-    __device__ static __forceinline__ void totals(const Acc &c, double *t) {
+    __device__ static __forceinline__ void fold(Acc &, int) {}
+    __device__ static __forceinline__ void flush(Acc &, double *, int) {}
+    __device__ static __forceinline__ void zero_totals(double *, int) {}
+    __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
         t[0] = c.gx; t[1] = c.gy; t[2] = c.gz; t[3] = c.hx; t[4] = c.hy; t[5] = c.hz; t[6] = c.gm;
     }
-    __device__ static __forceinline__ void nn(const Acc &, const unsigned char *, int64_t, double &d, int &id) {
+    __device__ static __forceinline__ void nn(const Acc &, const Sink &, const unsigned char *, int64_t, int, double &d,
+                                              int &id) {
         d = d_inf();
         id = -1;
     }
@@ -541,26 +593,34 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
                                           typename P::real eps2) {
     const unsigned char *base = st + lj * P::RB;
     const int step = jl * P::RB;
-#pragma unroll 4
-    for (int q = 0; q < per; ++q) {
-        const typename P::Rec r = P::ld_shared(base + q * step);
-        const int j = tb + q * jl + lj;
+    for (int q0 = 0; q0 < per; q0 += P::kChunk) {
+        const int jb = tb + q0 * jl + lj;  // this thread's first source of the chunk
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) P::template interact<SELF>(r, j, sk[k], ac[k], eps2);
+        for (int u = 0; u < P::kChunk; ++u) {
+            const typename P::Rec r = P::ld_shared(base + (q0 + u) * step);
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) P::template interact<SELF>(r, jb + u * jl, u, sk[k], ac[k], eps2);
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb);
     }
 }
 
+// Shared memory: kStages tiles of records, then (mixed policies) the FP64
+// totals, [sink k][field f][thread] so each thread owns its slots.
 template <class P, int IPT>
 __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_item;
     const int tid = threadIdx.x;
+    const int nt = blockDim.x;
     const int jl = p.jl;
     const int lj = tid & (jl - 1);
     const int islot = tid / jl;
-    const int slots = blockDim.x / jl;
+    const int slots = nt / jl;
     const typename P::real eps2 = static_cast<typename P::real>(p.eps2);
-    const int per = p.tile / jl;
+    const int per = p.tile / jl;  // a multiple of P::kChunk (host-checked)
+    double *tot = reinterpret_cast<double *>(smem + static_cast<size_t>(kStages) * p.tile * P::RB) + tid;
 
     for (;;) {
         __syncthreads();
@@ -588,6 +648,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             P::load_sink(p.rec, slot, sk[k]);
             sk[k].slot = val[k] ? slot : -1;
             P::init(ac[k]);
+            P::zero_totals(tot + k * P::NS * nt, nt);
         }
         const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
         const int64_t j1 = (j0 + p.slice_len < p.j_end) ? j0 + p.slice_len : p.j_end;
@@ -615,7 +676,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             since_flush += per;
             if (since_flush >= P::kFlush) {
 #pragma unroll
-                for (int k = 0; k < IPT; ++k) P::flush(ac[k]);
+                for (int k = 0; k < IPT; ++k) P::flush(ac[k], tot + k * P::NS * nt, nt);
                 since_flush = 0;
             }
         }
@@ -623,12 +684,12 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
 
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
-            P::flush(ac[k]);
+            P::flush(ac[k], tot + k * P::NS * nt, nt);
             double t[P::NS];
-            P::totals(ac[k], t);
+            P::totals(ac[k], tot + k * P::NS * nt, nt, t);
             double nd;
             int nid;
-            P::nn(ac[k], p.rec, p.j_end, nd, nid);
+            P::nn(ac[k], sk[k], p.rec, p.j_end, jl, nd, nid);
             for (int off = jl >> 1; off > 0; off >>= 1) {
 #pragma unroll
                 for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
@@ -720,8 +781,11 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
 // ---------------------------------------------------------------------------
 template <class P>
 __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams b) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const typename P::real eps2 = static_cast<typename P::real>(b.eps2);
+    double *tot = reinterpret_cast<double *>(smem) + threadIdx.x;
+    const int nt = blockDim.x;
     for (;;) {
         unsigned int item = 0;
         if (lane == 0) item = atomicAdd(b.queue, 1u);
@@ -735,20 +799,31 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
         P::load_sink(b.rec, slot, sk);
         sk.slot = val ? slot : -1;
         P::init(ac);
+        P::zero_totals(tot, nt);
         const unsigned char *src = b.rec + static_cast<int64_t>(it.x) * P::RB;
-        int since = 0;
-#pragma unroll 4
-        for (int q = 0; q < it.y; ++q) {
-            const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
-            P::template interact<true>(r, it.x + q, sk, ac, eps2);
-            if (++since == P::kFlush) { P::flush(ac); since = 0; }
+        int q = 0, since = 0;
+        for (; q + P::kChunk <= it.y; q += P::kChunk) {
+#pragma unroll
+            for (int u = 0; u < P::kChunk; ++u) {
+                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q + u) * P::RB);
+                P::template interact<true>(r, it.x + q + u, u, sk, ac, eps2);
+            }
+            P::fold(ac, it.x + q);
+            since += P::kChunk;
+            if (since >= P::kFlush) { P::flush(ac, tot, nt); since = 0; }
         }
-        P::flush(ac);
+        const int q0 = q;
+        for (; q < it.y; ++q) {
+            const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
+            P::template interact<true>(r, it.x + q, q - q0, sk, ac, eps2);
+        }
+        P::fold(ac, it.x + q0);
+        P::flush(ac, tot, nt);
         double t[P::NS];
-        P::totals(ac, t);
+        P::totals(ac, tot, nt, t);
         double nd;
         int nid;
-        P::nn(ac, b.rec, static_cast<int64_t>(it.x) + it.y, nd, nid);
+        P::nn(ac, sk, b.rec, static_cast<int64_t>(it.x) + it.y, 1, nd, nid);
         if (val) P::write_final(b, static_cast<int64_t>(slot) - b.out_base, t, nd, nid);
     }
 }
@@ -756,11 +831,22 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // ---------------------------------------------------------------------------
 // Instantiation helpers for one (order, precision) translation unit.
 // ---------------------------------------------------------------------------
+// Dynamic shared memory of a pass launch: the record ring plus, for the mixed
+// policies, the FP64 totals of every (thread, sink, field).
 template <class P, int IPT>
-inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t smem, cudaStream_t s) {
+inline size_t pass_smem(size_t ring_bytes, int threads) {
+    return ring_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
+}
+
+constexpr int kMaxDynSmem = 200 * 1024;
+
+template <class P, int IPT>
+inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t ring_bytes, cudaStream_t s) {
     static bool attr_set = false;
+    const size_t smem = pass_smem<P, IPT>(ring_bytes, threads);
+    if (smem > static_cast<size_t>(kMaxDynSmem)) return cudaErrorInvalidConfiguration;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -769,8 +855,13 @@ inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size
 }
 
 template <class P, int IPT>
-inline cudaError_t occupancy_pass(int threads, size_t smem, int *blocks) {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+inline cudaError_t occupancy_pass(int threads, size_t ring_bytes, int *blocks) {
+    const size_t smem = pass_smem<P, IPT>(ring_bytes, threads);
+    if (smem > static_cast<size_t>(kMaxDynSmem)) {
+        *blocks = 0;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT>, threads, smem);
 }
@@ -800,14 +891,19 @@ inline cudaError_t launch_reduce(const ReduceParams &r, cudaStream_t s) {
 }
 
 template <class P>
+inline size_t batched_smem(int threads) {
+    return P::kSmemTotals ? static_cast<size_t>(threads) * P::NS * sizeof(double) : 0;
+}
+
+template <class P>
 inline cudaError_t launch_batched(const BatchParams &b, int grid, int threads, cudaStream_t s) {
-    batched_kernel<P><<<grid, threads, 0, s>>>(b);
+    batched_kernel<P><<<grid, threads, batched_smem<P>(threads), s>>>(b);
     return cudaGetLastError();
 }
 
 template <class P>
 inline cudaError_t occupancy_batched(int threads, int *blocks) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<P>, threads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<P>, threads, batched_smem<P>(threads));
 }
 
 }  // namespace sp2

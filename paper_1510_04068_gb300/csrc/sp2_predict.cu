@@ -86,10 +86,23 @@ __global__ void predict_kernel(JStore js, int64_t n, double t, unsigned char *re
     const double dt4 = dmul(dt3, dt);
     const double h2 = dmul(dt2, c2), h3 = dmul(dt3, c3), h4 = dmul(dt4, c4);
     double xp[3], vp[3], ap[3];
+    // Mixed-precision records: Horner form with fused multiply-adds (the
+    // double-single split keeps ~48 bits, far more than the evaluation order
+    // changes).  FP64 records: left-to-right sums of explicitly rounded
+    // products, exactly the plain IEEE evaluation of the Taylor polynomial.
+    const double d2 = 0.5 * dt, d3 = dt * (1.0 / 6.0), d4 = dt * (1.0 / 24.0);
     for (int c = 0; c < 3; ++c) {
         const int64_t q = 3 * j + c;
         const double x = js.x[q], v = js.v[q], a = js.a[q], jk = js.jk[q];
-        if (ORDER == 6) {
+        if (MIXED && ORDER == 6) {
+            const double s = js.sn[q];
+            xp[c] = fma(fma(fma(fma(s, d4, jk * (1.0 / 6.0)), dt, 0.5 * a), dt, v), dt, x);
+            vp[c] = fma(fma(fma(s, d3, 0.5 * jk), dt, a), dt, v);
+            ap[c] = fma(fma(s, d2, jk), dt, a);
+        } else if (MIXED) {
+            xp[c] = fma(fma(fma(jk, d3, 0.5 * a), dt, v), dt, x);
+            vp[c] = fma(fma(jk, d2, a), dt, v);
+        } else if (ORDER == 6) {
             const double s = js.sn[q];
             xp[c] = dadd(dadd(dadd(dadd(x, dmul(v, dt)), dmul(a, h2)), dmul(jk, h3)), dmul(s, h4));
             vp[c] = dadd(dadd(dadd(v, dmul(a, dt)), dmul(jk, h2)), dmul(s, h3));

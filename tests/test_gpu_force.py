@@ -52,7 +52,7 @@ SHAPES = [
     dict(threads=128, i_per_thread=4, j_lanes=1, j_tile=256, split_j=5, ctas_per_sm=0),
     dict(threads=64, i_per_thread=1, j_lanes=4, j_tile=64, split_j=7, ctas_per_sm=2),
     dict(threads=128, i_per_thread=2, j_lanes=8, j_tile=128, split_j=40, ctas_per_sm=0),
-    dict(threads=32, i_per_thread=1, j_lanes=32, j_tile=64, split_j=64, ctas_per_sm=0),
+    dict(threads=32, i_per_thread=1, j_lanes=32, j_tile=256, split_j=64, ctas_per_sm=0),
     dict(threads=256, i_per_thread=4, j_lanes=2, j_tile=32, split_j=2, ctas_per_sm=1),
     dict(threads=64, i_per_thread=2, j_lanes=16, j_tile=256, split_j=33, ctas_per_sm=0),
 ]
