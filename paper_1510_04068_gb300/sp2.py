@@ -78,6 +78,8 @@ _SIGS = [
     ("sp2_profile_read", [_P, POINTER(c_int64), POINTER(c_double), c_int], c_int),
     ("sp2_kernel_launches", [_P], c_int64),
     ("sp2_info", [_P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int)], c_int),
+    ("sp2_step_static", [c_int64, _P, _P, _P, _P, _P, _P, _P, c_double, c_double, c_int64, _P, _P, _P, _P, _P, _P,
+                         _P], c_int),
     ("sp2_strerror", [c_int], c_char_p),
     ("sp2_last_error", [_P, c_char_p, c_size_t], c_int),
 ]
@@ -278,6 +280,23 @@ def sp2_profile_read(ctx):
     tot = (c_double * len(STAGES))()
     _check(load().sp2_profile_read(ctx, cnt, tot, len(STAGES)), ctx)
     return {STAGES[k]: (int(cnt[k]), float(tot[k])) for k in range(len(STAGES))}
+
+
+def sp2_step_static(inputs, t, eps2, i_idx, out, cuda_stream=None):
+    """Allocation-free mixed Hermite-4 block step on device tensors.
+
+    inputs = [id, m, x, v, a, jerk, t_j] of the sources; out = dict with acc,
+    jerk, pot and optionally nn_id, nn_r2.  All work is enqueued on cuda_stream
+    (None: the legacy default stream); the library's fixed scratch array is
+    shared by every call, so calls must not overlap on the GPU."""
+    ids = inputs[0]
+    ptrs, kind, _k = _marshal(list(inputs) + [i_idx, out.get("acc"), out.get("jerk"), out.get("pot"),
+                                                out.get("nn_id"), out.get("nn_r2")],
+                              [I4, F8, F8, F8, F8, F8, F8, I4, F8, F8, F8, I4, F8])
+    if kind != SP2_DEVICE:
+        raise TypeError("sp2_step_static takes device tensors")
+    st = load().sp2_step_static(len(ids), *ptrs[:7], float(t), float(eps2), len(i_idx), *ptrs[7:], cuda_stream)
+    _check(st)
 
 
 def sp2_kernel_launches(ctx) -> int:
