@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=131072)
@@ -106,7 +106,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -440,6 +440,15 @@ def extras(sp2, w, n, eps2, dev, stream):
                     gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), reps, stream)
                     sp2.sp2_graph_destroy(g)
                     row["mixed_graph_us_per_step"] = 1e3 * gms
+                    if na <= 1024:
+                        # the paper's 1D form: one thread per sink, no source split
+                        tuned_shape = c.get_launch(na)
+                        c.set_launch(na, dict(threads=max(32, min(256, 32 * ((na + 31) // 32))), i_per_thread=1,
+                                              j_lanes=1, j_tile=128, split_j=1, ctas_per_sm=0))
+                        ms1 = timed(fn, 3, stream)
+                        c.set_launch(na, tuned_shape)
+                        row["mixed_1d_us_per_step"] = 1e3 * ms1
+                        row["split_speedup_vs_1d"] = ms1 / ms
             row["mixed_over_fp64"] = row["mixed_interactions_per_s"] / row["fp64_interactions_per_s"]
             res["sweep"].append(row)
         for c in ctxs.values():
@@ -500,6 +509,10 @@ def bench_adjoint(dev, stream):
     x0, v0, mm = T(x).requires_grad_(True), T(v).requires_grad_(True), T(m).requires_grad_(True)
     ww = T(w)
     sim = AG.HermiteSim(n, eps2=1e-6, precision="mixed", stream=stream)
+    # one untimed pass loads every kernel module the trajectory uses
+    xw, _ = sim.trajectory(x0, v0, mm, dt, 2, checkpoint_every=1)
+    (ww * xw).sum().backward()
+    x0.grad = v0.grad = mm.grad = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     xf, vf = sim.trajectory(x0, v0, mm, dt, steps, checkpoint_every=8)

@@ -492,13 +492,15 @@ sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg) {
     c->js.a = static_cast<double *>(dalloc(c, n3));
     c->js.jk = static_cast<double *>(dalloc(c, n3));
     c->js.sn = cfg->order == 6 ? static_cast<double *>(dalloc(c, n3)) : nullptr;
+    c->js.dsc = mixed ? static_cast<float4 *>(dalloc(c, n * dscache_words(cfg->order) * sizeof(float4))) : nullptr;
     c->rec = static_cast<unsigned char *>(dalloc(c, n * c->rb));
     c->rec2 = static_cast<unsigned char *>(dalloc(c, n * std::max(vjp_record_bytes(0), vjp_record_bytes(1))));
     c->iota = static_cast<int32_t *>(dalloc(c, n * sizeof(int32_t)));
     c->tmp = static_cast<double *>(dalloc(c, 4 * n3));
     c->dev_words = static_cast<unsigned int *>(dalloc(c, 64));
     const bool ok = c->js.id && c->js.m && c->js.t && c->js.x && c->js.v && c->js.a && c->js.jk &&
-                    (cfg->order == 4 || c->js.sn) && c->rec && c->rec2 && c->iota && c->tmp && c->dev_words;
+                    (cfg->order == 4 || c->js.sn) && (!mixed || c->js.dsc) && c->rec && c->rec2 && c->iota &&
+                    c->tmp && c->dev_words;
     if (!ok) {
         while (!c->owned.empty()) dfree(c, c->owned.back());
         delete c;
@@ -580,6 +582,12 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
             SP2_CK(c, cudaMemcpyAsync(c->js.a + 3 * o, a, n3, cudaMemcpyHostToDevice, c->stream));
             SP2_CK(c, cudaMemcpyAsync(c->js.jk + 3 * o, jerk, n3, cudaMemcpyHostToDevice, c->stream));
             if (snap) SP2_CK(c, cudaMemcpyAsync(c->js.sn + 3 * o, snap, n3, cudaMemcpyHostToDevice, c->stream));
+            if (c->js.dsc) {
+                ev_begin(c, ST_OTHER);
+                SP2_CK(c, launch_dscache(c->cfg.order, c->js, first, n, c->stream));
+                ev_end(c, ST_OTHER);
+                c->launches += 1;
+            }
             SP2_CK(c, cudaStreamSynchronize(c->stream));
         } else {
             Staging s{c};
@@ -609,6 +617,12 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
             SP2_CK(c, cudaMemcpyAsync(c->js.a + 3 * o, a, n3, cudaMemcpyDeviceToDevice, c->stream));
             SP2_CK(c, cudaMemcpyAsync(c->js.jk + 3 * o, jerk, n3, cudaMemcpyDeviceToDevice, c->stream));
             if (snap) SP2_CK(c, cudaMemcpyAsync(c->js.sn + 3 * o, snap, n3, cudaMemcpyDeviceToDevice, c->stream));
+            if (c->js.dsc) {
+                ev_begin(c, ST_OTHER);
+                SP2_CK(c, launch_dscache(c->cfg.order, c->js, first, n, c->stream));
+                ev_end(c, ST_OTHER);
+                c->launches += 1;
+            }
         } else {
             ev_begin(c, ST_OTHER);
             SP2_CK(c, launch_scatter_j(c->js, slots, n, c->n_loaded, c->dev_words + 1, id, m, x, v, a, jerk, snap, t, c->stream));

@@ -15,7 +15,14 @@ namespace sp2 {
 struct JStore {
     int32_t *id;
     double *m, *x, *v, *a, *jk, *sn, *t;  // x/v/a/jk/sn: n x 3 row-major
+    // Mixed-precision contexts also keep a double-single copy of each particle
+    // (null otherwise), written whenever the FP64 store is, so that the
+    // per-step predictor needs no FP64 arithmetic:
+    //   {xh yh zh m}{xl yl zl th}{vxh vyh vzh tl}{vxl vyl vzl id}
+    //   {axh ayh azh 0}{axl ayl azl 0}{jx jy jz 0}[{sx sy sz 0}]   (float4 words)
+    float4 *dsc;
 };
+inline int dscache_words(int order) { return order == 6 ? 8 : 7; }
 
 // Bytes of one predicted record.
 //   mixed H4: {xh yh zh m}{xl yl zl id}{vx vy vz 0}            48 B
@@ -126,8 +133,12 @@ cudaError_t launch_scatter_j(const JStore &dst, const int32_t *slots, int64_t n,
                              unsigned int *err, const int32_t *id, const double *m, const double *x,
                              const double *v, const double *a, const double *jk, const double *sn,
                              const double *t, cudaStream_t s);
+// Mixed records come from js.dsc when it is set (double-single arithmetic),
+// from the FP64 arrays otherwise.
 cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, double t,
                            unsigned char *rec, cudaStream_t s);
+// Refresh js.dsc for slots [first, first + n) from the FP64 store.
+cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n, cudaStream_t s);
 // (m, x, v) -> order-4 records with no prediction (all-pairs entry points)
 cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const double *x,
                               const double *v, unsigned char *rec, cudaStream_t s);

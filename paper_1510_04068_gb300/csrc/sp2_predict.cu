@@ -53,6 +53,105 @@ __device__ __forceinline__ void store_fp64(unsigned char *rec, int rb, int64_t j
     }
 }
 
+// ---- double-single arithmetic (Dekker 1971; Knuth's TwoSum; TwoProd by FMA).
+// Every step is explicitly rounded so no multiply-add is fused behind our back.
+struct ds {
+    float h, l;
+};
+__device__ __forceinline__ ds two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ds fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ds ds_add(ds a, ds b) {
+    ds s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ds ds_add_f(ds a, float b) {
+    ds s = two_sum(a.h, b);
+    return fast_two_sum(s.h, __fadd_rn(s.l, a.l));
+}
+__device__ __forceinline__ ds ds_mul(ds a, ds b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ds ds_split(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - static_cast<double>(h))};
+}
+
+__device__ __forceinline__ void write_dscache(const JStore &d, int64_t s) {
+    float4 *o = d.dsc + s * ((d.sn != nullptr) ? 8 : 7);
+    const ds x0 = ds_split(d.x[3 * s]), x1 = ds_split(d.x[3 * s + 1]), x2 = ds_split(d.x[3 * s + 2]);
+    const ds v0 = ds_split(d.v[3 * s]), v1 = ds_split(d.v[3 * s + 1]), v2 = ds_split(d.v[3 * s + 2]);
+    const ds a0 = ds_split(d.a[3 * s]), a1 = ds_split(d.a[3 * s + 1]), a2 = ds_split(d.a[3 * s + 2]);
+    const ds tt = ds_split(d.t[s]);
+    o[0] = make_float4(x0.h, x1.h, x2.h, __double2float_rn(d.m[s]));
+    o[1] = make_float4(x0.l, x1.l, x2.l, tt.h);
+    o[2] = make_float4(v0.h, v1.h, v2.h, tt.l);
+    o[3] = make_float4(v0.l, v1.l, v2.l, __int_as_float(d.id[s]));
+    o[4] = make_float4(a0.h, a1.h, a2.h, 0.f);
+    o[5] = make_float4(a0.l, a1.l, a2.l, 0.f);
+    o[6] = make_float4(__double2float_rn(d.jk[3 * s]), __double2float_rn(d.jk[3 * s + 1]),
+                       __double2float_rn(d.jk[3 * s + 2]), 0.f);
+    if (d.sn)
+        o[7] = make_float4(__double2float_rn(d.sn[3 * s]), __double2float_rn(d.sn[3 * s + 1]),
+                           __double2float_rn(d.sn[3 * s + 2]), 0.f);
+}
+
+__global__ void dscache_kernel(JStore d, int64_t first, int64_t n) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k < n) write_dscache(d, first + k);
+}
+
+// Mixed-precision predictor on the double-single cache.  Positions:
+//   x_p = x + dt (v + dt (a/2 + dt (j/6 [+ dt s/24])))
+// with x, v, a/2 and dt as double-single values and the jerk / snap terms in
+// FP32 (they enter multiplied by dt^3, far below the double-single
+// resolution of x); velocities and accelerations leave as FP32 values.
+template <int ORDER>
+__global__ void predict_ds_kernel(const float4 *dsc, int64_t n, float t_hi, float t_lo, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    constexpr int W = (ORDER == 6) ? 8 : 7;
+    const float4 *q = dsc + j * W;
+    const float4 w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4], w5 = q[5], w6 = q[6];
+    float4 w7 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ORDER == 6) w7 = q[7];
+    const ds dt = ds_add({t_hi, t_lo}, {-w1.w, -w2.w});
+    const float xh[3] = {w0.x, w0.y, w0.z}, xl[3] = {w1.x, w1.y, w1.z};
+    const float vh[3] = {w2.x, w2.y, w2.z}, vl[3] = {w3.x, w3.y, w3.z};
+    const float ah[3] = {w4.x, w4.y, w4.z}, al[3] = {w5.x, w5.y, w5.z};
+    const float jk[3] = {w6.x, w6.y, w6.z}, sn[3] = {w7.x, w7.y, w7.z};
+    float oh[3], ol[3], ov[3], oa[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        // innermost FP32 terms: j/6 (+ dt s/24) for x, j/2 (+ dt s/6) for v, j (+ dt s/2) for a
+        const float jx = (ORDER == 6) ? fmaf(dt.h * (1.f / 24.f), sn[c], jk[c] * (1.f / 6.f)) : jk[c] * (1.f / 6.f);
+        const ds cx = ds_add_f({0.5f * ah[c], 0.5f * al[c]}, dt.h * jx);
+        const ds bx = ds_add({vh[c], vl[c]}, ds_mul(dt, cx));
+        const ds px = ds_add({xh[c], xl[c]}, ds_mul(dt, bx));
+        oh[c] = px.h;
+        ol[c] = px.l;
+        const float jv = (ORDER == 6) ? fmaf(dt.h * (1.f / 6.f), sn[c], 0.5f * jk[c]) : 0.5f * jk[c];
+        ov[c] = vh[c] + fmaf(dt.h, fmaf(dt.h, jv, ah[c] + al[c]), vl[c]);
+        if (ORDER == 6) oa[c] = ah[c] + fmaf(dt.h, fmaf(dt.h, 0.5f * sn[c], jk[c]), al[c]);
+    }
+    const int rb = (ORDER == 6) ? 64 : 48;
+    float4 *o = reinterpret_cast<float4 *>(rec + j * rb);
+    o[0] = make_float4(oh[0], oh[1], oh[2], w0.w);
+    o[1] = make_float4(ol[0], ol[1], ol[2], w3.w);
+    o[2] = make_float4(ov[0], ov[1], ov[2], 0.f);
+    if (ORDER == 6) o[3] = make_float4(oa[0], oa[1], oa[2], 0.f);
+}
+
 __global__ void scatter_kernel(JStore d, const int32_t *slots, int64_t n, int64_t n_loaded, unsigned int *err,
                                const int32_t *id, const double *m, const double *x, const double *v,
                                const double *a, const double *jk, const double *sn, const double *t) {
@@ -73,6 +172,7 @@ __global__ void scatter_kernel(JStore d, const int32_t *slots, int64_t n, int64_
         d.jk[3 * s + c] = jk[3 * k + c];
         if (sn) d.sn[3 * s + c] = sn[3 * k + c];
     }
+    if (d.dsc) write_dscache(d, s);
 }
 
 template <int ORDER, bool MIXED>
@@ -250,10 +350,24 @@ cudaError_t launch_scatter_j(const JStore &dst, const int32_t *slots, int64_t n,
     return cudaGetLastError();
 }
 
+cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n, cudaStream_t s) {
+    if (n <= 0 || !js.dsc) return cudaSuccess;
+    (void)order;
+    dscache_kernel<<<grid_for(n), kThreads, 0, s>>>(js, first, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, double t, unsigned char *rec,
                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned g = grid_for(n);
+    if (mixed && js.dsc) {
+        const float th = static_cast<float>(t);
+        const float tl = static_cast<float>(t - static_cast<double>(th));
+        if (order == 6) predict_ds_kernel<6><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
+        else predict_ds_kernel<4><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
+        return cudaGetLastError();
+    }
     if (order == 6) {
         if (mixed) predict_kernel<6, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
         else predict_kernel<6, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
