@@ -134,7 +134,9 @@ struct MixedForce {
     // the low 3 mantissa bits carry the source's position u in the chunk (a
     // 2^-20 relative truncation, far inside the 1e-5 tie band) and one unsigned
     // min per interaction keeps the chunk's best.
-    template <bool SELF>
+    // FIRST: the first source of a chunk starts the level-1 partials (assigns
+    // instead of accumulating, so folding needs no zeroing).
+    template <bool SELF, bool FIRST>
     __device__ static __forceinline__ void interact(const Rec &r, int j, int u, const Sink &s, Acc &c, float eps2) {
         const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
         const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
@@ -146,16 +148,16 @@ struct MixedForce {
         const float rinv2 = rinv * rinv;
         const float mr = r.w[0].w * rinv;
         const float mr3 = mr * rinv2;
-        c.f[NS - 1] += mr;
+        c.f[NS - 1] = FIRST ? mr : c.f[NS - 1] + mr;
         const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
         const float al3 = 3.f * (rv * rinv2);
         if (ORDER == 4) {
-            c.f[0] = fmaf(mr3, dx, c.f[0]);
-            c.f[1] = fmaf(mr3, dy, c.f[1]);
-            c.f[2] = fmaf(mr3, dz, c.f[2]);
-            c.f[3] = fmaf(mr3, fmaf(-al3, dx, dvx), c.f[3]);
-            c.f[4] = fmaf(mr3, fmaf(-al3, dy, dvy), c.f[4]);
-            c.f[5] = fmaf(mr3, fmaf(-al3, dz, dvz), c.f[5]);
+            c.f[0] = FIRST ? mr3 * dx : fmaf(mr3, dx, c.f[0]);
+            c.f[1] = FIRST ? mr3 * dy : fmaf(mr3, dy, c.f[1]);
+            c.f[2] = FIRST ? mr3 * dz : fmaf(mr3, dz, c.f[2]);
+            c.f[3] = FIRST ? mr3 * fmaf(-al3, dx, dvx) : fmaf(mr3, fmaf(-al3, dx, dvx), c.f[3]);
+            c.f[4] = FIRST ? mr3 * fmaf(-al3, dy, dvy) : fmaf(mr3, fmaf(-al3, dy, dvy), c.f[4]);
+            c.f[5] = FIRST ? mr3 * fmaf(-al3, dz, dvz) : fmaf(mr3, fmaf(-al3, dz, dvz), c.f[5]);
         } else {
             const float dax = r.w[3].x - s.ax, day = r.w[3].y - s.ay, daz = r.w[3].z - s.az;
             const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
@@ -167,24 +169,31 @@ struct MixedForce {
             const float al = rv * rinv2;
             const float b3 = 3.f * fmaf(vv + ra, rinv2, al * al);
             const float a6 = 2.f * al3;
-            c.f[0] += Ax; c.f[1] += Ay; c.f[2] += Az;
-            c.f[3] += Jx; c.f[4] += Jy; c.f[5] += Jz;
-            c.f[6] += fmaf(mr3, dax, -fmaf(a6, Jx, b3 * Ax));
-            c.f[7] += fmaf(mr3, day, -fmaf(a6, Jy, b3 * Ay));
-            c.f[8] += fmaf(mr3, daz, -fmaf(a6, Jz, b3 * Az));
+            const float Sx = fmaf(mr3, dax, -fmaf(a6, Jx, b3 * Ax));
+            const float Sy = fmaf(mr3, day, -fmaf(a6, Jy, b3 * Ay));
+            const float Sz = fmaf(mr3, daz, -fmaf(a6, Jz, b3 * Az));
+            if (FIRST) {
+                c.f[0] = Ax; c.f[1] = Ay; c.f[2] = Az;
+                c.f[3] = Jx; c.f[4] = Jy; c.f[5] = Jz;
+                c.f[6] = Sx; c.f[7] = Sy; c.f[8] = Sz;
+            } else {
+                c.f[0] += Ax; c.f[1] += Ay; c.f[2] += Az;
+                c.f[3] += Jx; c.f[4] += Jy; c.f[5] += Jz;
+                c.f[6] += Sx; c.f[7] += Sy; c.f[8] += Sz;
+            }
         }
         if (NN) {
             const unsigned key = (SELF && j == s.slot) ? 0xffffffffu : ((__float_as_uint(d2) & ~7u) | unsigned(u));
-            c.ck = min(c.ck, key);
+            c.ck = FIRST ? key : min(c.ck, key);
         }
     }
     // end of a chunk whose first source (for this thread) is slot `base`
     __device__ static __forceinline__ void fold(Acc &c, int base) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) { c.g[f] += c.f[f]; c.f[f] = 0.f; }
-        if (NN) {
-            if (c.ck < c.bk) { c.bk = c.ck; c.bbase = base; }
-            c.ck = 0xffffffffu;
+        for (int f = 0; f < NS; ++f) c.g[f] += c.f[f];
+        if (NN && c.ck < c.bk) {
+            c.bk = c.ck;
+            c.bbase = base;
         }
     }
     // level 2 -> FP64 totals tot[f * stride]
@@ -286,7 +295,7 @@ struct Fp64Force {
         c.nn_d2 = d_inf();
         c.nn_id = -1;
     }
-    template <bool SELF>
+    template <bool SELF, bool FIRST>
     __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, double eps2) {
         const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
         const double m = r.w[1].y;
@@ -406,7 +415,7 @@ struct MixedVjp {
 #pragma unroll
         for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = 0.f;
     }
-    template <bool SELF>
+    template <bool SELF, bool FIRST>
     __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, float eps2) {
         const float dx = (r.w[0].x - s.xh) + (r.w[1].x - s.xl);
         const float dy = (r.w[0].y - s.yh) + (r.w[1].y - s.yl);
@@ -430,17 +439,19 @@ struct MixedVjp {
         const float cv = 3.f * s2 * D;
         const float cr = 3.f * s2 * (q1 * B1 - q2 * B2) - 6.f * al * s2 * D - s3 * fmaf(s.pb, ml, pl * s.m);
         const float t1 = 3.f * al * q1, t2 = 3.f * al * q2;
-        c.f[0] += q2 * abx - q1 * s.abx + t1 * s.jbx - t2 * jbx + cv * vx + cr * dx;
-        c.f[1] += q2 * aby - q1 * s.aby + t1 * s.jby - t2 * jby + cv * vy + cr * dy;
-        c.f[2] += q2 * abz - q1 * s.abz + t1 * s.jbz - t2 * jbz + cv * vz + cr * dz;
-        c.f[3] += q2 * jbx - q1 * s.jbx + cv * dx;
-        c.f[4] += q2 * jby - q1 * s.jby + cv * dy;
-        c.f[5] += q2 * jbz - q1 * s.jbz + cv * dz;
-        c.f[6] -= fmaf(s3, B2, pl * rinv);
+        const float t[NS] = {q2 * abx - q1 * s.abx + t1 * s.jbx - t2 * jbx + cv * vx + cr * dx,
+                             q2 * aby - q1 * s.aby + t1 * s.jby - t2 * jby + cv * vy + cr * dy,
+                             q2 * abz - q1 * s.abz + t1 * s.jbz - t2 * jbz + cv * vz + cr * dz,
+                             q2 * jbx - q1 * s.jbx + cv * dx,
+                             q2 * jby - q1 * s.jby + cv * dy,
+                             q2 * jbz - q1 * s.jbz + cv * dz,
+                             -fmaf(s3, B2, pl * rinv)};
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.f[f] = FIRST ? t[f] : c.f[f] + t[f];
     }
     __device__ static __forceinline__ void fold(Acc &c, int) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) { c.g[f] += c.f[f]; c.f[f] = 0.f; }
+        for (int f = 0; f < NS; ++f) c.g[f] += c.f[f];
     }
     __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
 #pragma unroll
@@ -517,7 +528,7 @@ struct Fp64Vjp {
         s.jbx = r.w[5].y; s.jby = r.w[6].x; s.jbz = r.w[6].y;
     }
     __device__ static __forceinline__ void init(Acc &c) { c.gx = c.gy = c.gz = c.hx = c.hy = c.hz = c.gm = 0.0; }
-    template <bool SELF>
+    template <bool SELF, bool FIRST>
     __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, double eps2) {
         const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
         const double vx = r.w[2].x - s.vx, vy = r.w[2].y - s.vy, vz = r.w[3].x - s.vz;
@@ -595,11 +606,16 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
     const int step = jl * P::RB;
     for (int q0 = 0; q0 < per; q0 += P::kChunk) {
         const int jb = tb + q0 * jl + lj;  // this thread's first source of the chunk
+        {
+            const typename P::Rec r = P::ld_shared(base + q0 * step);
 #pragma unroll
-        for (int u = 0; u < P::kChunk; ++u) {
+            for (int k = 0; k < IPT; ++k) P::template interact<SELF, true>(r, jb, 0, sk[k], ac[k], eps2);
+        }
+#pragma unroll
+        for (int u = 1; u < P::kChunk; ++u) {
             const typename P::Rec r = P::ld_shared(base + (q0 + u) * step);
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) P::template interact<SELF>(r, jb + u * jl, u, sk[k], ac[k], eps2);
+            for (int k = 0; k < IPT; ++k) P::template interact<SELF, false>(r, jb + u * jl, u, sk[k], ac[k], eps2);
         }
 #pragma unroll
         for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb);
@@ -803,21 +819,31 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
         const unsigned char *src = b.rec + static_cast<int64_t>(it.x) * P::RB;
         int q = 0, since = 0;
         for (; q + P::kChunk <= it.y; q += P::kChunk) {
+            {
+                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
+                P::template interact<true, true>(r, it.x + q, 0, sk, ac, eps2);
+            }
 #pragma unroll
-            for (int u = 0; u < P::kChunk; ++u) {
+            for (int u = 1; u < P::kChunk; ++u) {
                 const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q + u) * P::RB);
-                P::template interact<true>(r, it.x + q + u, u, sk, ac, eps2);
+                P::template interact<true, false>(r, it.x + q + u, u, sk, ac, eps2);
             }
             P::fold(ac, it.x + q);
             since += P::kChunk;
             if (since >= P::kFlush) { P::flush(ac, tot, nt); since = 0; }
         }
-        const int q0 = q;
-        for (; q < it.y; ++q) {
-            const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
-            P::template interact<true>(r, it.x + q, q - q0, sk, ac, eps2);
+        if (q < it.y) {  // ragged end: a shorter last chunk
+            const int q0 = q;
+            {
+                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
+                P::template interact<true, true>(r, it.x + q, 0, sk, ac, eps2);
+            }
+            for (++q; q < it.y; ++q) {
+                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
+                P::template interact<true, false>(r, it.x + q, q - q0, sk, ac, eps2);
+            }
+            P::fold(ac, it.x + q0);
         }
-        P::fold(ac, it.x + q0);
         P::flush(ac, tot, nt);
         double t[P::NS];
         P::totals(ac, tot, nt, t);
