@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--n", type=int, default=131072)
     p.add_argument("--n-active", type=int, default=131072)
     p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint lines")
+    p.add_argument("--extras", default="sweep,h6,batched,adjoint",
+                   help="comma-separated secondary sections to run: sweep, h6, batched, adjoint")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
@@ -353,7 +355,7 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         line["e2e"] = e2e(ctx, w, upd, out, args, stream)
     if not args.no_extras and rank == 0:
-        line["detail"] = extras(sp2, w, n, eps2, dev, stream)
+        line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -401,61 +403,116 @@ def timed(fn, reps, stream):
     return statistics.median(ts)
 
 
-def extras(sp2, w, n, eps2, dev, stream):
+def extras(sp2, w, n, eps2, dev, stream, sections):
     """N_active sweep (mixed vs FP64), batched systems, adjoint: secondary lines."""
     import torch
     D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
-    res = {"sweep": []}
-    full = {k: D(w[k]) for k in ("ids", "m", "x", "v", "a", "jerk", "tj")}
+    res = {}
     with torch.cuda.stream(stream):
-        ctxs = {}
-        for prec in (sp2.SP2_MIXED, sp2.SP2_FP64):
-            c = sp2.Context(order=4, precision=prec, n_max=n, eps2=eps2, cuda_stream=stream.cuda_stream)
-            c.set_j(0, full["ids"], full["m"], full["x"], full["v"], full["a"], full["jerk"], None, full["tj"])
-            c.predict(w["t"])
-            ctxs[prec] = c
-        for na in (1, 8, 64, 1024, 16384, 131072):
-            idx = D(W.active_set(n, na, 1000 + na))
-            o = dict(acc=torch.empty((na, 3), dtype=torch.float64, device=dev),
-                     jerk=torch.empty((na, 3), dtype=torch.float64, device=dev),
-                     pot=torch.empty(na, dtype=torch.float64, device=dev),
-                     nn_id=torch.empty(na, dtype=torch.int32, device=dev),
-                     nn_r2=torch.empty(na, dtype=torch.float64, device=dev))
-            row = {"n_active": na}
-            for prec, name in ((sp2.SP2_MIXED, "mixed"), (sp2.SP2_FP64, "fp64")):
-                c = ctxs[prec]
-                if name == "fp64" and na > 16384:
-                    reps = 2
-                else:
-                    reps = 20
-                c.autotune(na) if (name == "mixed" or na <= 1024) else None
-                fn = lambda: (c.predict(w["t"]), c.compute(idx, **o))  # noqa: E731
-                ms = timed(fn, reps, stream)
-                row[f"{name}_us_per_step"] = 1e3 * ms
-                row[f"{name}_interactions_per_s"] = na * n / (ms / 1e3)
-                if name == "mixed":
-                    sp2.sp2_graph_begin(c.ctx)
-                    fn()
-                    g = sp2.sp2_graph_end(c.ctx)
-                    gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), reps, stream)
-                    sp2.sp2_graph_destroy(g)
-                    row["mixed_graph_us_per_step"] = 1e3 * gms
-                    if na <= 1024:
-                        # the paper's 1D form: one thread per sink, no source split
-                        tuned_shape = c.get_launch(na)
-                        c.set_launch(na, dict(threads=max(32, min(256, 32 * ((na + 31) // 32))), i_per_thread=1,
-                                              j_lanes=1, j_tile=128, split_j=1, ctas_per_sm=0))
-                        ms1 = timed(fn, 3, stream)
-                        c.set_launch(na, tuned_shape)
-                        row["mixed_1d_us_per_step"] = 1e3 * ms1
-                        row["split_speedup_vs_1d"] = ms1 / ms
-            row["mixed_over_fp64"] = row["mixed_interactions_per_s"] / row["fp64_interactions_per_s"]
-            res["sweep"].append(row)
-        for c in ctxs.values():
-            c.close()
-        res["batched"] = bench_batched(sp2, dev, stream)
-        res["adjoint"] = bench_adjoint(dev, stream)
+        if "sweep" in sections:
+            res["sweep"] = sweep(sp2, w, n, eps2, dev, stream)
+        if "h6" in sections:
+            res["h6"] = bench_h6(sp2, dev, stream)
+        if "batched" in sections:
+            res["batched"] = bench_batched(sp2, dev, stream)
+        if "adjoint" in sections:
+            res["adjoint"] = bench_adjoint(dev, stream)
     return res
+
+
+def sweep(sp2, w, n, eps2, dev, stream):
+    """interactions/s per block step vs N_active, mixed and FP64."""
+    import torch
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    rows = []
+    full = {k: D(w[k]) for k in ("ids", "m", "x", "v", "a", "jerk", "tj")}
+    ctxs = {}
+    for prec in (sp2.SP2_MIXED, sp2.SP2_FP64):
+        c = sp2.Context(order=4, precision=prec, n_max=n, eps2=eps2, cuda_stream=stream.cuda_stream)
+        c.set_j(0, full["ids"], full["m"], full["x"], full["v"], full["a"], full["jerk"], None, full["tj"])
+        c.predict(w["t"])
+        ctxs[prec] = c
+    for na in (1, 8, 64, 1024, 16384, 131072):
+        idx = D(W.active_set(n, na, 1000 + na))
+        o = dict(acc=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 jerk=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 pot=torch.empty(na, dtype=torch.float64, device=dev),
+                 nn_id=torch.empty(na, dtype=torch.int32, device=dev),
+                 nn_r2=torch.empty(na, dtype=torch.float64, device=dev))
+        row = {"n_active": na}
+        for prec, name in ((sp2.SP2_MIXED, "mixed"), (sp2.SP2_FP64, "fp64")):
+            c = ctxs[prec]
+            if name == "fp64" and na > 16384:
+                reps = 2
+            else:
+                reps = 20
+            c.autotune(na) if (name == "mixed" or na <= 1024) else None
+            fn = lambda: (c.predict(w["t"]), c.compute(idx, **o))  # noqa: E731
+            ms = timed(fn, reps, stream)
+            row[f"{name}_us_per_step"] = 1e3 * ms
+            row[f"{name}_interactions_per_s"] = na * n / (ms / 1e3)
+            if name == "mixed":
+                sp2.sp2_graph_begin(c.ctx)
+                fn()
+                g = sp2.sp2_graph_end(c.ctx)
+                gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), reps, stream)
+                sp2.sp2_graph_destroy(g)
+                row["mixed_graph_us_per_step"] = 1e3 * gms
+                if na <= 1024:
+                    # the paper's 1D form: one thread per sink, no source split
+                    tuned_shape = c.get_launch(na)
+                    c.set_launch(na, dict(threads=max(32, min(256, 32 * ((na + 31) // 32))), i_per_thread=1,
+                                          j_lanes=1, j_tile=128, split_j=1, ctas_per_sm=0))
+                    ms1 = timed(fn, 3, stream)
+                    c.set_launch(na, tuned_shape)
+                    row["mixed_1d_us_per_step"] = 1e3 * ms1
+                    row["split_speedup_vs_1d"] = ms1 / ms
+        row["mixed_over_fp64"] = row["mixed_interactions_per_s"] / row["fp64_interactions_per_s"]
+        rows.append(row)
+    for c in ctxs.values():
+        c.close()
+    return rows
+
+
+def bench_h6(sp2, dev, stream):
+    """Hermite-6 on a Salpeter Plummer sphere, N = 65536: mixed vs FP64."""
+    import torch
+    n = 65536
+    m, x, v = W.plummer(n, 3)
+    m = W.salpeter_masses(n, 10)
+    a, jk, sn = W.derivative_noise(n, 16, scales=(1.0, 4.0, 16.0))
+    ids = W.particle_ids(n)
+    tj = W.block_times(n, 14, 0.5)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    rows = []
+    ctxs = {}
+    for prec in (sp2.SP2_MIXED, sp2.SP2_FP64):
+        c = sp2.Context(order=6, precision=prec, n_max=n, eps2=1e-8, cuda_stream=stream.cuda_stream)
+        c.set_j(0, D(ids), D(m), D(x), D(v), D(a), D(jk), D(sn), D(tj))
+        c.predict(0.5)
+        ctxs[prec] = c
+    for na in (32, 4096, 65536):
+        idx = D(W.active_set(n, na, 2000 + na))
+        o = dict(acc=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 jerk=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 snap=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 pot=torch.empty(na, dtype=torch.float64, device=dev),
+                 nn_id=torch.empty(na, dtype=torch.int32, device=dev),
+                 nn_r2=torch.empty(na, dtype=torch.float64, device=dev))
+        row = {"n_active": na}
+        for prec, name in ((sp2.SP2_MIXED, "mixed"), (sp2.SP2_FP64, "fp64")):
+            c = ctxs[prec]
+            if name == "mixed" or na <= 4096:
+                c.autotune(na)
+            fn = lambda: (c.predict(0.5), c.compute(idx, **o))  # noqa: E731
+            ms = timed(fn, 2 if (name == "fp64" and na > 4096) else 10, stream)
+            row[f"{name}_us_per_step"] = 1e3 * ms
+            row[f"{name}_interactions_per_s"] = na * n / (ms / 1e3)
+        row["mixed_over_fp64"] = row["mixed_interactions_per_s"] / row["fp64_interactions_per_s"]
+        rows.append(row)
+    for c in ctxs.values():
+        c.close()
+    return rows
 
 
 def bench_batched(sp2, dev, stream):

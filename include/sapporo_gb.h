@@ -108,7 +108,8 @@ sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg);
 sp2_status sp2_close(sp2_ctx *ctx);
 
 /* Copy kernel (Sec. 2.2.4, "copy kernel"): store n j-particles.
- *  slots == NULL: into slots first .. first+n-1 (first + n <= n_max); the loaded
+ *  slots == NULL: into slots first .. first+n-1 (first <= loaded count, so the
+ *                 loaded slots stay contiguous; first + n <= n_max); the loaded
  *                 count becomes max(loaded, first + n).
  *  slots != NULL: particle k goes to slot slots[k] (int32, each < loaded count;
  *                 `first` is ignored); used to update the active particles of a

@@ -563,6 +563,9 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
     if (!slots) {
         if (first < 0 || first + n > c->cfg.n_max) return fail(c, SP2_ERR_RANGE, "slots [%lld, %lld) exceed n_max %lld",
                                                                  (long long)first, (long long)(first + n), (long long)c->cfg.n_max);
+        if (first > c->n_loaded)
+            return fail(c, SP2_ERR_RANGE, "first slot %lld would leave slots [%lld, %lld) unloaded", (long long)first,
+                        (long long)c->n_loaded, (long long)first);
     } else {
         if (n > c->n_loaded) return fail(c, SP2_ERR_RANGE, "more slots than loaded particles");
         if (ptr_kind == SP2_HOST)
@@ -951,74 +954,98 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     if (nn && 9 * c->cfg.n_max + 3 * n_i > 12 * c->cfg.n_max) o.nn_r2 = nullptr, o.nn_id = nullptr;
 
     const sp2_launch h = heuristic(c, K_FORCE, mixed, n_i, n_j);
-    std::vector<sp2_launch> cand;
-    auto add = [&](sp2_launch L) {
-        if (L.threads / L.j_lanes * L.i_per_thread > 2 * std::max<int64_t>(n_i, 32) && L.threads > 32) return;
-        if (check_launch(c, L) != SP2_OK) return;
-        for (auto &q : cand)
-            if (std::memcmp(&q, &L, sizeof L) == 0) return;
-        cand.push_back(L);
+    // time one launch shape: mean of `reps` runs after one warm-up run
+    auto time_shape = [&](const sp2_launch &L, int reps, float *ms_out) -> sp2_status {
+        if (check_launch(c, L) != SP2_OK) return SP2_ERR_UNSUPPORTED;
+        float ms = 0.f, sum = 0.f;
+        sp2_status st = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i,
+                                 0, n_j, o, &L, ST_FORCE, &ms);
+        if (st != SP2_OK) return st;
+        for (int r = 0; r < reps; ++r) {
+            st = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j,
+                          o, &L, ST_FORCE, &ms);
+            if (st != SP2_OK) return st;
+            sum += ms;
+        }
+        *ms_out = sum / reps;
+        return SP2_OK;
     };
-    const int ipts[3] = {1, 2, 4};
-    const int tiles[4] = {64, 128, 256, 512};
+    // resident CTAs per SM of a shape (0 if it does not fit)
+    auto occupancy = [&](const sp2_launch &L) -> int {
+        int occ = 0;
+        const size_t ring = static_cast<size_t>(kStagesDevice) * L.j_tile * c->rb;
+        const size_t tot = mixed ? static_cast<size_t>(L.threads) * L.i_per_thread * (order == 6 ? 10 : 7) * 8 : 0;
+        KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread};
+        if (ring + tot > 200 * 1024 || force_kernel_occupancy(key, L.threads, ring, &occ) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return occ;
+    };
+    // split counts that give about `rounds` waves of resident CTAs, preferring
+    // an exact multiple (a partial last wave leaves SMs idle)
+    const int64_t max_split_all = std::max<int64_t>(1, n_j / 32);
+    auto split_for = [&](const sp2_launch &L, int rounds, int occ) -> int {
+        const int64_t n_iblk = ceil_div(n_i, int64_t(L.threads / L.j_lanes) * L.i_per_thread);
+        const int64_t slots = int64_t(c->sm_count) * occ;
+        const int64_t max_split = std::min<int64_t>(max_split_all, std::max<int64_t>(1, n_j / (2 * L.j_tile)));
+        int64_t split = ceil_div(rounds * slots, n_iblk);
+        for (int64_t s2 = split; s2 <= split + 2 && s2 <= max_split; ++s2)
+            if ((n_iblk * s2) % slots == 0) { split = s2; break; }
+        return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(split, max_split)));
+    };
+    // stage 1: CTA shapes at ~4 waves
+    std::vector<std::pair<float, sp2_launch>> shapes;
     for (int threads : {64, 128, 256})
-        for (int ipt : ipts)
+        for (int ipt : {1, 2, 4})
             for (int jl = 1; jl <= 32; jl *= 2) {
                 if (jl > threads) continue;
                 const int64_t spc = int64_t(threads / jl) * ipt;
-                const int64_t n_iblk = ceil_div(n_i, spc);
-                // skip shapes that leave the GPU mostly idle or split the sinks far too finely
-                if (n_iblk * threads < int64_t(c->sm_count) * 32 && jl < 32 && threads * ipt / jl < n_i) continue;
-                if (jl > 1 && n_i * jl / ipt > int64_t(c->sm_count) * 4096) continue;
-                for (int tile : tiles) {
+                if (spc > 2 * std::max<int64_t>(n_i, 32) && threads > 32) continue;   // mostly empty CTAs
+                if (jl > 1 && spc < 8 && n_i > 4096) continue;                       // j-lanes only help few sinks
+                for (int tile : {64, 128, 256, 512}) {
                     if (tile < 8 * jl) continue;
-                    const int64_t slots = int64_t(c->sm_count) * std::max(1, 512 / threads);
-                    for (int mult : {1, 2, 4, 8}) {
-                        sp2_launch L{threads, ipt, jl, tile, 1, 0};
-                        int64_t split = ceil_div(mult * slots, n_iblk);
-                        split = std::max<int64_t>(1, std::min<int64_t>(split, n_j / (2 * tile)));
-                        if (n_iblk >= 4 * slots) split = (mult == 1) ? 1 : std::min<int64_t>(mult / 2 + 1, n_j / (2 * tile));
-                        L.split_j = static_cast<int>(std::max<int64_t>(1, split));
-                        add(L);
-                    }
+                    sp2_launch L{threads, ipt, jl, tile, 1, 0};
+                    const int occ = occupancy(L);
+                    if (occ <= 0) continue;
+                    L.split_j = split_for(L, 4, occ);
+                    float ms = 0.f;
+                    const sp2_status st = time_shape(L, 1, &ms);
+                    if (st == SP2_ERR_UNSUPPORTED) continue;
+                    if (st != SP2_OK) return st;
+                    shapes.push_back({ms, L});
                 }
             }
-    add(h);
-    // bound the search time: coarse pass of one run each, then the best few again
-    std::vector<std::pair<float, size_t>> t1;
-    const int64_t work = n_i * n_j;
-    const size_t max_cand = work > (int64_t(1) << 32) ? 24 : 400;
-    if (cand.size() > max_cand) {
-        // keep the heuristic and an even sample of the rest
-        std::vector<sp2_launch> keep{h};
-        const size_t stride = cand.size() / max_cand + 1;
-        for (size_t k = 0; k < cand.size(); k += stride) keep.push_back(cand[k]);
-        cand.swap(keep);
+    {
+        float ms = 0.f;
+        if (time_shape(h, 1, &ms) == SP2_OK) shapes.push_back({ms, h});
     }
+    if (shapes.empty()) return fail(c, SP2_ERR_UNSUPPORTED, "no launch shape could run");
+    std::sort(shapes.begin(), shapes.end(), [](const std::pair<float, sp2_launch> &x, const std::pair<float, sp2_launch> &y) {
+        return x.first < y.first;
+    });
+    // stage 2: the best shapes over 1 .. 16 waves, three timed runs each
+    std::vector<sp2_launch> cand;
+    for (size_t r = 0; r < std::min<size_t>(4, shapes.size()); ++r) {
+        const sp2_launch base = shapes[r].second;
+        const int occ = occupancy(base);
+        cand.push_back(base);
+        for (int rounds : {1, 2, 3, 6, 8, 12, 16}) {
+            sp2_launch L = base;
+            L.split_j = split_for(L, rounds, occ);
+            bool dup = false;
+            for (auto &q : cand) dup |= std::memcmp(&q, &L, sizeof L) == 0;
+            if (!dup) cand.push_back(L);
+        }
+    }
+    size_t best_k = 0;
+    float best_ms = 1e30f;
     for (size_t k = 0; k < cand.size(); ++k) {
         float ms = 0.f;
-        sp2_status s = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j, o, &cand[k], ST_FORCE, &ms);
-        if (s == SP2_ERR_UNSUPPORTED) continue;
-        if (s != SP2_OK) return s;
-        s = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j, o, &cand[k], ST_FORCE, &ms);
-        if (s != SP2_OK) return s;
-        t1.push_back({ms, k});
-    }
-    if (t1.empty()) return fail(c, SP2_ERR_UNSUPPORTED, "no launch shape could run");
-    std::sort(t1.begin(), t1.end());
-    size_t best_k = t1[0].second;
-    float best_ms = 1e30f;
-    for (size_t r = 0; r < std::min<size_t>(4, t1.size()); ++r) {
-        float sum = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-            float ms = 0.f;
-            SP2_CKS(run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j, o, &cand[t1[r].second], ST_FORCE, &ms));
-            sum += ms;
-        }
-        if (sum < best_ms) {
-            best_ms = sum;
-            best_k = t1[r].second;
-        }
+        const sp2_status st = time_shape(cand[k], 3, &ms);
+        if (st == SP2_ERR_UNSUPPORTED) continue;
+        if (st != SP2_OK) return st;
+        if (ms < best_ms) { best_ms = ms; best_k = k; }
     }
     c->tuned[bucket_of(n_i)] = cand[best_k];
     if (best) *best = cand[best_k];

@@ -73,6 +73,7 @@ struct MixedForce {
     static constexpr bool kSmemTotals = true;
     static constexpr int kChunk = 8;
     static constexpr int kFlush = 64;
+    static constexpr unsigned kKeyMask = kChunk - 1;  // low r^2 bits carrying the in-chunk position
     typedef float real;
     struct Rec {
         float4 w[NW];
@@ -131,9 +132,9 @@ struct MixedForce {
     }
     // fields: 0-2 acc, 3-5 jerk, [6-8 snap], NS-1 potential (accumulated as +m/r).
     // Nearest neighbour: r^2 >= 0, so its bit pattern orders like the value;
-    // the low 3 mantissa bits carry the source's position u in the chunk (a
-    // 2^-20 relative truncation, far inside the 1e-5 tie band) and one unsigned
-    // min per interaction keeps the chunk's best.
+    // the low log2(kChunk) mantissa bits carry the source's position u in the
+    // chunk (a 2^-20 relative truncation for 8, far inside the 1e-5 tie band)
+    // and one unsigned min per interaction keeps the chunk's best.
     // FIRST: the first source of a chunk starts the level-1 partials (assigns
     // instead of accumulating, so folding needs no zeroing).
     template <bool SELF, bool FIRST>
@@ -183,7 +184,7 @@ struct MixedForce {
             }
         }
         if (NN) {
-            const unsigned key = (SELF && j == s.slot) ? 0xffffffffu : ((__float_as_uint(d2) & ~7u) | unsigned(u));
+            const unsigned key = (SELF && j == s.slot) ? 0xffffffffu : ((__float_as_uint(d2) & ~kKeyMask) | unsigned(u));
             c.ck = FIRST ? key : min(c.ck, key);
         }
     }
@@ -215,8 +216,8 @@ struct MixedForce {
     // the bound keeps the lookup inside the record array regardless).
     __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
                                               int jl, double &d, int &id) {
-        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & 7u) * jl : -1;
-        if (NN && j >= 0 && j < limit && (c.bk & ~7u) < 0x7f800000u) {
+        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
+        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
             const Rec r = ld_global(rec + j * RB);
             d = static_cast<double>(dist2(r, s));
             id = __float_as_int(r.w[1].w);
@@ -795,13 +796,37 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
 // warp-uniform (broadcast) loads that stay in L1 while the chunks of one
 // system are processed.
 // ---------------------------------------------------------------------------
+constexpr int kBatchTile = 64;  // sources per warp-private shared-memory tile
+
+template <class P, bool SELF>
+__device__ __forceinline__ void batch_tile_loop(const unsigned char *st, int tb, int n, const typename P::Sink &sk,
+                                                typename P::Acc &ac, typename P::real eps2) {
+    for (int q0 = 0; q0 < n; q0 += P::kChunk) {
+        {
+            const typename P::Rec r = P::ld_shared(st + q0 * P::RB);
+            P::template interact<SELF, true>(r, tb + q0, 0, sk, ac, eps2);
+        }
+#pragma unroll
+        for (int u = 1; u < P::kChunk; ++u) {
+            const typename P::Rec r = P::ld_shared(st + (q0 + u) * P::RB);
+            P::template interact<SELF, false>(r, tb + q0 + u, u, sk, ac, eps2);
+        }
+        P::fold(ac, tb + q0);
+    }
+}
+
+// Warps take (system, up-to-32-sink chunk) items from the device queue in the
+// plan's cost order; one sink per lane.  The system's sources pass through a
+// warp-private shared-memory tile filled with coalesced 16-byte loads (ragged
+// ends padded with filler records), then are read as broadcasts.  FP64 totals
+// stay in registers (systems are short).
 template <class P>
 __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams b) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
+    unsigned char *wbuf = smem + static_cast<size_t>(threadIdx.x >> 5) * kBatchTile * P::RB;
     const typename P::real eps2 = static_cast<typename P::real>(b.eps2);
-    double *tot = reinterpret_cast<double *>(smem) + threadIdx.x;
-    const int nt = blockDim.x;
+    constexpr int W = P::RB / 16;
     for (;;) {
         unsigned int item = 0;
         if (lane == 0) item = atomicAdd(b.queue, 1u);
@@ -815,38 +840,35 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
         P::load_sink(b.rec, slot, sk);
         sk.slot = val ? slot : -1;
         P::init(ac);
-        P::zero_totals(tot, nt);
-        const unsigned char *src = b.rec + static_cast<int64_t>(it.x) * P::RB;
-        int q = 0, since = 0;
-        for (; q + P::kChunk <= it.y; q += P::kChunk) {
-            {
-                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
-                P::template interact<true, true>(r, it.x + q, 0, sk, ac, eps2);
-            }
+        double tot[P::NS];
 #pragma unroll
-            for (int u = 1; u < P::kChunk; ++u) {
-                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q + u) * P::RB);
-                P::template interact<true, false>(r, it.x + q + u, u, sk, ac, eps2);
+        for (int f = 0; f < P::NS; ++f) tot[f] = 0.0;
+        const unsigned char *src = b.rec + static_cast<int64_t>(it.x) * P::RB;
+        int since = 0;
+        for (int t0 = 0; t0 < it.y; t0 += kBatchTile) {
+            const int cnt = min(kBatchTile, it.y - t0);
+            const int padded = (cnt + P::kChunk - 1) / P::kChunk * P::kChunk;
+            __syncwarp();
+            for (int c = lane; c < padded * W; c += 32) {
+                uint4 w4;
+                if (c < cnt * W) w4 = __ldg(reinterpret_cast<const uint4 *>(src + static_cast<int64_t>(t0) * P::RB) + c);
+                else w4 = P::sentinel(c % W);
+                *reinterpret_cast<uint4 *>(wbuf + 16 * c) = w4;
             }
-            P::fold(ac, it.x + q);
-            since += P::kChunk;
-            if (since >= P::kFlush) { P::flush(ac, tot, nt); since = 0; }
+            __syncwarp();
+            const int tb = it.x + t0;
+            const bool mine = val && slot >= tb && slot < tb + cnt;
+            if (__any_sync(kFull, mine)) batch_tile_loop<P, true>(wbuf, tb, padded, sk, ac, eps2);
+            else batch_tile_loop<P, false>(wbuf, tb, padded, sk, ac, eps2);
+            since += padded;
+            if (since >= P::kFlush) {
+                P::flush(ac, tot, 1);
+                since = 0;
+            }
         }
-        if (q < it.y) {  // ragged end: a shorter last chunk
-            const int q0 = q;
-            {
-                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
-                P::template interact<true, true>(r, it.x + q, 0, sk, ac, eps2);
-            }
-            for (++q; q < it.y; ++q) {
-                const typename P::Rec r = P::ld_global(src + static_cast<int64_t>(q) * P::RB);
-                P::template interact<true, false>(r, it.x + q, q - q0, sk, ac, eps2);
-            }
-            P::fold(ac, it.x + q0);
-        }
-        P::flush(ac, tot, nt);
+        P::flush(ac, tot, 1);
         double t[P::NS];
-        P::totals(ac, tot, nt, t);
+        P::totals(ac, tot, 1, t);
         double nd;
         int nid;
         P::nn(ac, sk, b.rec, static_cast<int64_t>(it.x) + it.y, 1, nd, nid);
@@ -918,7 +940,7 @@ inline cudaError_t launch_reduce(const ReduceParams &r, cudaStream_t s) {
 
 template <class P>
 inline size_t batched_smem(int threads) {
-    return P::kSmemTotals ? static_cast<size_t>(threads) * P::NS * sizeof(double) : 0;
+    return static_cast<size_t>(threads / 32) * kBatchTile * P::RB;
 }
 
 template <class P>

@@ -128,6 +128,11 @@ def test_call_order_and_range_errors(env):
     c.compute(ok, acc=acc2)
     c.sync()
     assert torch.allclose(acc2, acc[[0, 3]], rtol=1e-5, atol=0)
+    # a contiguous store may not leave a gap of unloaded slots
+    with pytest.raises(sp2.SP2Error) as e:
+        one0 = {k: D(s[k][:1]) for k in ("ids", "m", "x", "v", "a", "jerk", "tj")}
+        c.set_j(501, one0["ids"], one0["m"], one0["x"], one0["v"], one0["a"], one0["jerk"], None, one0["tj"])
+    assert e.value.status == -2
     # device-side scatter slots out of range
     one = {k: D(s[k][:1]) for k in ("ids", "m", "x", "v", "a", "jerk", "tj")}
     c.set_j(0, one["ids"], one["m"], one["x"], one["v"], one["a"], one["jerk"], None, one["tj"],
