@@ -125,8 +125,12 @@ sp2_status sp2_set_j(sp2_ctx *ctx, int64_t first, int64_t n, const int32_t *slot
 /* Predictor (Sec. 2.2.4 "predict" kernel; Hermite predictor of Makino & Aarseth
  * 1992 / Nitadori & Makino 2008): Taylor-expand every loaded j-particle from its
  * own t_j to t and write the predicted records used by sp2_compute (FP64
- * records, or double-single records in SP2_MIXED).  dt^k/k! is formed as
- * dt^k times the double nearest 1/k!, sums left to right.
+ * records, or double-single records in SP2_MIXED).  FP64: dt^k/k! is formed as
+ * dt^k times the double nearest 1/k!, sums left to right.  SP2_MIXED evaluates
+ * the polynomial in double-single arithmetic from a double-single copy of the
+ * store, and defers the work: the next sp2_compute with few enough sinks
+ * predicts its sources inside the force pass, any other consumer writes the
+ * records first.  Results do not depend on which happens.
  * Errors: SP2_ERR_STATE (nothing loaded), SP2_ERR_ARG (t not finite). */
 sp2_status sp2_predict(sp2_ctx *ctx, double t);
 

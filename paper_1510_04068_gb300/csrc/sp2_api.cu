@@ -54,7 +54,9 @@ struct sp2_ctx {
     JStore js{};
     int64_t n_loaded = 0;
     unsigned char *rec = nullptr;   // predicted records
-    bool rec_valid = false;
+    bool rec_valid = false;         // sp2_predict has been called since the last sp2_set_j
+    bool pred_pending = false;      // mixed: records not yet written for t_pred (written on demand)
+    double t_pred = 0.0;
     unsigned char *rec2 = nullptr;  // records of the all-pairs / VJP entry points
     int32_t *iota = nullptr;
     double *tmp = nullptr;          // 4 x (n_max x 3) doubles: a1, j1, xpbar, vpbar
@@ -152,6 +154,17 @@ void ev_end(sp2_ctx *c, int st) {
     c->ev_count[st] += 1;
 }
 
+// Write the predicted records of a deferred sp2_predict (mixed contexts).
+sp2_status materialize(sp2_ctx *c) {
+    if (!c->pred_pending) return SP2_OK;
+    ev_begin(c, ST_PREDICT);
+    SP2_CK(c, launch_predict(c->cfg.order, 1, c->js, c->n_loaded, c->t_pred, c->rec, c->stream));
+    ev_end(c, ST_PREDICT);
+    c->launches += 1;
+    c->pred_pending = false;
+    return SP2_OK;
+}
+
 // Grow-only device buffer; refused while a graph is being captured.
 sp2_status ensure(sp2_ctx *c, void **buf, size_t *cap, size_t need, const char *what) {
     if (need <= *cap) return SP2_OK;
@@ -230,10 +243,15 @@ struct PassOut {
     int accumulate = 0;
 };
 
-// rec holds n_valid records; sink slots must lie in [0, n_valid).
+// rec holds n_valid records; sink slots must lie in [0, n_valid).  With
+// allow_fused (the context's own records, mixed precision) a launch whose sinks
+// fit one i-block predicts its sources from the double-single cache inside the
+// pass (each source is predicted once); otherwise deferred records are written
+// first.
 sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const unsigned char *rec, int rb,
                     int64_t n_valid, const int32_t *i_idx, int64_t n_i, int64_t j_begin, int64_t j_end,
-                    const PassOut &o, const sp2_launch *forced, int stage_force, float *ms_out = nullptr) {
+                    const PassOut &o, const sp2_launch *forced, int stage_force, float *ms_out = nullptr,
+                    bool allow_fused = false) {
     if (n_i <= 0) return SP2_OK;
     sp2_launch L;
     if (forced) {
@@ -243,11 +261,13 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         L = (it != c->tuned.end()) ? it->second : heuristic(c, kind, mixed, n_i, j_end - j_begin);
     }
     const int64_t n_j = j_end - j_begin;
-    KernelKey key{kind, order, mixed, nn, L.i_per_thread};
     const int jl = L.j_lanes;
     int tile = L.j_tile;
     const int64_t sinks_per_cta = static_cast<int64_t>(L.threads / jl) * L.i_per_thread;
     const int64_t n_iblk = ceil_div(n_i, sinks_per_cta);
+    const int fused = (allow_fused && kind == K_FORCE && mixed && c->js.dsc && n_iblk == 1) ? 1 : 0;
+    if (!fused && allow_fused) SP2_CKS(materialize(c));
+    KernelKey key{kind, order, mixed, nn, L.i_per_thread, fused};
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
@@ -284,6 +304,11 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     p.eps2 = c->cfg.eps2;
     p.acc = o.acc; p.jerk = o.jerk; p.snap = o.snap; p.pot = o.pot; p.nn_id = o.nn_id; p.nn_r2 = o.nn_r2;
     p.xbar = o.xbar; p.vbar = o.vbar; p.mbar = o.mbar; p.accumulate = o.accumulate;
+    if (fused) {
+        p.dsc = c->js.dsc;
+        p.t_hi = static_cast<float>(c->t_pred);
+        p.t_lo = static_cast<float>(c->t_pred - static_cast<double>(p.t_hi));
+    }
     const int ns = ns_fields;
     if (split > 1) {
         const size_t need = static_cast<size_t>(ns + (nn ? 1 : 0)) * split * n_i * sizeof(double);
@@ -292,6 +317,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
                                static_cast<size_t>(split) * n_i * sizeof(int32_t), "partial-id"));
         p.part = c->part;
         p.part_id = c->part_id;
+        p.sink_major = split >= kWarpReduceMinSplit ? 1 : 0;
     }
     SP2_CK(c, cudaMemsetAsync(c->dev_words, 0, sizeof(unsigned int), c->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -635,6 +661,7 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
     }
     if (!slots) c->n_loaded = std::max(c->n_loaded, first + n);
     c->rec_valid = false;
+    c->pred_pending = false;
     return SP2_OK;
 }
 
@@ -642,6 +669,12 @@ sp2_status sp2_predict(sp2_ctx *c, double t) {
     SP2_CKS(usable(c));
     if (!std::isfinite(t)) return fail(c, SP2_ERR_ARG, "t is not finite");
     if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
+    c->t_pred = t;
+    if (c->js.dsc) {  // mixed: records are written on demand, or predicted inside the pass
+        c->pred_pending = true;
+        c->rec_valid = true;
+        return SP2_OK;
+    }
     ev_begin(c, ST_PREDICT);
     SP2_CK(c, launch_predict(c->cfg.order, c->cfg.precision == SP2_MIXED, c->js, c->n_loaded, t, c->rec, c->stream));
     ev_end(c, ST_PREDICT);
@@ -688,7 +721,8 @@ sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t
         o.acc = acc; o.jerk = jerk; o.snap = snap; o.pot = pot; o.nn_id = nn_id; o.nn_r2 = nn_r2;
     }
     const int nn = c->cfg.with_nn && (o.nn_id || o.nn_r2);
-    SP2_CKS(run_pass(c, K_FORCE, c->cfg.order, mixed, nn, c->rec, c->rb, c->n_loaded, d_idx, n_i, j_begin, j_end, o, nullptr, ST_FORCE));
+    SP2_CKS(run_pass(c, K_FORCE, c->cfg.order, mixed, nn, c->rec, c->rb, c->n_loaded, d_idx, n_i, j_begin, j_end, o,
+                     nullptr, ST_FORCE, nullptr, true));
     const double *arrs[4] = {o.acc, o.jerk, o.snap, o.pot};
     const int64_t lens[4] = {3 * n_i, 3 * n_i, 3 * n_i, n_i};
     SP2_CKS(finite_check(c, arrs, lens, 4));
@@ -784,6 +818,7 @@ sp2_status sp2_compute_batched(sp2_ctx *c, const sp2_batch_plan *plan, double *a
     }
     const int mixed = c->cfg.precision == SP2_MIXED;
     const int nn = c->cfg.with_nn && (b.nn_id || b.nn_r2);
+    SP2_CKS(materialize(c));
     b.rec = c->rec;
     b.items = plan->items;
     b.n_items = plan->n_items;
@@ -959,11 +994,11 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         if (check_launch(c, L) != SP2_OK) return SP2_ERR_UNSUPPORTED;
         float ms = 0.f, sum = 0.f;
         sp2_status st = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i,
-                                 0, n_j, o, &L, ST_FORCE, &ms);
+                                 0, n_j, o, &L, ST_FORCE, &ms, true);
         if (st != SP2_OK) return st;
         for (int r = 0; r < reps; ++r) {
             st = run_pass(c, K_FORCE, order, mixed, nn && o.nn_id, c->rec, c->rb, c->n_loaded, c->iota, n_i, 0, n_j,
-                          o, &L, ST_FORCE, &ms);
+                          o, &L, ST_FORCE, &ms, true);
             if (st != SP2_OK) return st;
             sum += ms;
         }

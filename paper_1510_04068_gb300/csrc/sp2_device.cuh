@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sp2_ds.cuh"
 #include "sp2_internal.h"
 
 namespace sp2 {
@@ -74,6 +75,8 @@ struct MixedForce {
     static constexpr int kChunk = 8;
     static constexpr int kFlush = 64;
     static constexpr unsigned kKeyMask = kChunk - 1;  // low r^2 bits carrying the in-chunk position
+    static constexpr bool kCanFuse = true;
+    static constexpr int kOrder = ORDER;
     typedef float real;
     struct Rec {
         float4 w[NW];
@@ -108,6 +111,22 @@ struct MixedForce {
         if (w == 0) return f4bits(1e25f, 1e25f, 1e25f, 0.f);
         if (w == 1) return make_uint4(0u, 0u, 0u, 0xffffffffu);
         return make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the predicted record of source j, straight from the double-single cache
+    __device__ static __forceinline__ Rec predict(const float4 *dsc, int64_t j, float t_hi, float t_lo) {
+        float4 o[4];
+        predict_ds_record<ORDER>(dsc, j, t_hi, t_lo, o);
+        Rec r;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r.w[w] = o[w];
+        return r;
+    }
+    __device__ static __forceinline__ void sink_from(const Rec &r, Sink &s) {
+        s.xh = r.w[0].x; s.yh = r.w[0].y; s.zh = r.w[0].z;
+        s.xl = r.w[1].x; s.yl = r.w[1].y; s.zl = r.w[1].z;
+        s.vx = r.w[2].x; s.vy = r.w[2].y; s.vz = r.w[2].z;
+        if (ORDER == 6) { s.ax = r.w[3].x; s.ay = r.w[3].y; s.az = r.w[3].z; }
+        else { s.ax = s.ay = s.az = 0.f; }
     }
     __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
         const Rec r = ld_global(rec + slot * RB);
@@ -211,9 +230,23 @@ struct MixedForce {
         for (int f = 0; f < NS; ++f) t[f] = tot[f * stride];
         t[NS - 1] = -t[NS - 1];
     }
-    // The chosen source is slot bbase + u * jl; its r^2 is recomputed exactly.
-    // limit: one past the last real source slot (filler records never qualify,
-    // the bound keeps the lookup inside the record array regardless).
+    // The chosen source is slot bbase + u * jl; its r^2 is recomputed exactly
+    // from its record (read, or predicted again when fused).  limit: one past
+    // the last real source slot (filler records never qualify, the bound keeps
+    // the lookup inside the arrays regardless).
+    template <bool FUSED>
+    __device__ static __forceinline__ void nn_lookup(const Acc &c, const Sink &s, const ForceParams &p, int64_t limit,
+                                                     int jl, double &d, int &id) {
+        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
+        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
+            const Rec r = FUSED ? predict(p.dsc, j, p.t_hi, p.t_lo) : ld_global(p.rec + j * RB);
+            d = static_cast<double>(dist2(r, s));
+            id = __float_as_int(r.w[1].w);
+        } else {
+            d = d_inf();
+            id = -1;
+        }
+    }
     __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
                                               int jl, double &d, int &id) {
         const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
@@ -247,6 +280,7 @@ struct MixedForce {
 template <int ORDER, bool NN>
 struct Fp64Force {
     static constexpr int NW = (ORDER == 6) ? 6 : 4;
+    static constexpr bool kCanFuse = false;
     static constexpr int RB = NW * 16;
     static constexpr int NS = (ORDER == 6) ? 10 : 7;
     static constexpr bool kNN = NN;
@@ -370,6 +404,7 @@ struct Fp64Force {
 // ---------------------------------------------------------------------------
 struct MixedVjp {
     static constexpr int NW = 5;
+    static constexpr bool kCanFuse = false;
     static constexpr int RB = 80;
     static constexpr int NS = 7;
     static constexpr bool kNN = false;
@@ -487,6 +522,7 @@ struct MixedVjp {
 
 struct Fp64Vjp {
     static constexpr int NW = 7;
+    static constexpr bool kCanFuse = false;
     static constexpr int RB = 112;
     static constexpr int NS = 7;
     static constexpr bool kNN = false;
@@ -583,19 +619,34 @@ struct Fp64Vjp {
 // records so the inner loop has a fixed trip count.  Sinks whose own slot lies
 // in the current tile take the variant of the loop that skips the self pair.
 // ---------------------------------------------------------------------------
-template <class P>
+template <class P, bool FUSED>
 __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *smem, int t, int64_t j0, int64_t j1) {
     const int tile = p.tile;
     unsigned char *dst = smem + static_cast<size_t>(t % kStages) * tile * P::RB;
     const int64_t tb = j0 + static_cast<int64_t>(t) * tile;
     const int64_t rem = j1 - tb;
     const int cnt = rem < tile ? static_cast<int>(rem) : tile;
-    const unsigned char *src = p.rec + tb * P::RB;
     constexpr int W = P::RB / 16;
-    const int n16 = tile * W, v16 = cnt * W;
-    for (int c = threadIdx.x; c < n16; c += blockDim.x) {
-        if (c < v16) cp_async16(dst + 16 * c, src + 16 * static_cast<size_t>(c));
-        else *reinterpret_cast<uint4 *>(dst + 16 * c) = P::sentinel(c % W);
+    if constexpr (FUSED && P::kCanFuse) {
+        // predict the tile's sources from the double-single cache (one per thread)
+        for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+            uint4 *d = reinterpret_cast<uint4 *>(dst + static_cast<size_t>(c) * P::RB);
+            if (c < cnt) {
+                const typename P::Rec r = P::predict(p.dsc, tb + c, p.t_hi, p.t_lo);
+#pragma unroll
+                for (int w = 0; w < W; ++w) d[w] = *reinterpret_cast<const uint4 *>(&r.w[w]);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) d[w] = P::sentinel(w);
+            }
+        }
+    } else {
+        const unsigned char *src = p.rec + tb * P::RB;
+        const int n16 = tile * W, v16 = cnt * W;
+        for (int c = threadIdx.x; c < n16; c += blockDim.x) {
+            if (c < v16) cp_async16(dst + 16 * c, src + 16 * static_cast<size_t>(c));
+            else *reinterpret_cast<uint4 *>(dst + 16 * c) = P::sentinel(c % W);
+        }
     }
 }
 
@@ -625,7 +676,7 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
 
 // Shared memory: kStages tiles of records, then (mixed policies) the FP64
 // totals, [sink k][field f][thread] so each thread owns its slots.
-template <class P, int IPT>
+template <class P, int IPT, bool FUSED>
 __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_item;
@@ -662,7 +713,8 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
                 val[k] = false;
             }
             const int slot = val[k] ? raw : static_cast<int>(p.j_begin);
-            P::load_sink(p.rec, slot, sk[k]);
+            if constexpr (FUSED && P::kCanFuse) P::sink_from(P::predict(p.dsc, slot, p.t_hi, p.t_lo), sk[k]);
+            else P::load_sink(p.rec, slot, sk[k]);
             sk[k].slot = val[k] ? slot : -1;
             P::init(ac[k]);
             P::zero_totals(tot + k * P::NS * nt, nt);
@@ -673,14 +725,14 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
 
 #pragma unroll
         for (int s = 0; s < kStages - 1; ++s) {
-            if (s < n_tiles) load_tile<P>(p, smem, s, j0, j1);
+            if (s < n_tiles) load_tile<P, FUSED>(p, smem, s, j0, j1);
             cp_async_commit();
         }
         int since_flush = 0;
         for (int t = 0; t < n_tiles; ++t) {
             cp_async_wait<kStages - 2>();
             __syncthreads();
-            if (t + kStages - 1 < n_tiles) load_tile<P>(p, smem, t + kStages - 1, j0, j1);
+            if (t + kStages - 1 < n_tiles) load_tile<P, FUSED>(p, smem, t + kStages - 1, j0, j1);
             cp_async_commit();
             const unsigned char *st = smem + static_cast<size_t>(t % kStages) * p.tile * P::RB;
             const int tb = static_cast<int>(j0) + t * p.tile;
@@ -706,7 +758,8 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             P::totals(ac[k], tot + k * P::NS * nt, nt, t);
             double nd;
             int nid;
-            P::nn(ac[k], sk[k], p.rec, p.j_end, jl, nd, nid);
+            if constexpr (P::kCanFuse) P::template nn_lookup<FUSED>(ac[k], sk[k], p, p.j_end, jl, nd, nid);
+            else P::nn(ac[k], sk[k], p.rec, p.j_end, jl, nd, nid);
             for (int off = jl >> 1; off > 0; off >>= 1) {
 #pragma unroll
                 for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
@@ -719,6 +772,15 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             if (lj == 0 && val[k]) {
                 if (p.split == 1) {
                     P::write_final(p, ii[k], t, nd, nid);
+                } else if (p.sink_major) {
+                    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+                    double *base = p.part + ii[k] * NF * p.split + slice;
+#pragma unroll
+                    for (int f = 0; f < P::NS; ++f) base[f * p.split] = t[f];
+                    if (P::kNN) {
+                        base[P::NS * p.split] = nd;
+                        p.part_id[ii[k] * p.split + slice] = nid;
+                    }
                 } else {
                     const int64_t stride = static_cast<int64_t>(p.split) * p.n_i;
                     double *base = p.part + static_cast<int64_t>(slice) * p.n_i + ii[k];
@@ -756,25 +818,27 @@ __global__ void reduce_kernel(const ReduceParams r) {
     P::write_final(r, i, t, nd, nid);
 }
 
-// The same reduction with one warp per sink, for many slices (small n_i): lane
-// l sums slices l, l+32, ... in order, then a fixed xor-butterfly combines the
-// lanes, so the result is still independent of scheduling.
+// The same reduction with one warp per sink, for many slices, on the
+// sink-major layout (a warp's loads are contiguous): lane l sums slices l,
+// l+32, ... in order, then a fixed xor-butterfly combines the lanes, so the
+// result is still independent of scheduling.
 template <class P>
 __global__ void reduce_warp_kernel(const ReduceParams r) {
     const int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= r.n_i) return;  // uniform across the warp
-    const int64_t stride = static_cast<int64_t>(r.split) * r.n_i;
+    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+    const double *row = r.part + i * NF * r.split;
+    const int32_t *row_id = r.part_id + i * r.split;
     double t[P::NS];
 #pragma unroll
     for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
     double nd = d_inf();
     int nid = -1;
     for (int s = lane; s < r.split; s += 32) {
-        const double *base = r.part + static_cast<int64_t>(s) * r.n_i + i;
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += base[f * stride];
-        if (P::kNN) nn_merge(nd, nid, base[P::NS * stride], r.part_id[static_cast<int64_t>(s) * r.n_i + i]);
+        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
+        if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -787,6 +851,62 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
         }
     }
     if (lane == 0) P::write_final(r, i, t, nd, nid);
+}
+
+// Few sinks, many slices: one 256-thread block per sink on the sink-major
+// layout.  Thread t sums slices t, t+256, ... in order; a fixed xor-butterfly
+// combines each warp and warp 0 adds the eight warp sums in order, so the
+// result does not depend on scheduling.  Many threads per sink keep many
+// loads in flight (a single warp walking 1000+ slices is latency bound).
+template <class P>
+__global__ void __launch_bounds__(256) reduce_block_kernel(const ReduceParams r) {
+    __shared__ double s_t[8][P::NS];
+    __shared__ double s_d[8];
+    __shared__ int s_id[8];
+    const int64_t i = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+    const double *row = r.part + i * NF * r.split;
+    const int32_t *row_id = r.part_id + i * r.split;
+    double t[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    double nd = d_inf();
+    int nid = -1;
+    for (int s = tid; s < r.split; s += 256) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
+        if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+        if (P::kNN) {
+            const double od = __shfl_xor_sync(kFull, nd, off);
+            const int oid = __shfl_xor_sync(kFull, nid, off);
+            nn_merge(nd, nid, od, oid);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) s_t[warp][f] = t[f];
+        s_d[warp] = nd;
+        s_id[warp] = nid;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] = s_t[0][f];
+        nd = s_d[0];
+        nid = s_id[0];
+        for (int w = 1; w < 8; ++w) {
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) t[f] += s_t[w][f];
+            if (P::kNN) nn_merge(nd, nid, s_d[w], s_id[w]);
+        }
+        P::write_final(r, i, t, nd, nid);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -888,47 +1008,63 @@ inline size_t pass_smem(size_t ring_bytes, int threads) {
 
 constexpr int kMaxDynSmem = 200 * 1024;
 
-template <class P, int IPT>
+template <class P, int IPT, bool FUSED>
 inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t ring_bytes, cudaStream_t s) {
     static bool attr_set = false;
     const size_t smem = pass_smem<P, IPT>(ring_bytes, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) return cudaErrorInvalidConfiguration;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxDynSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    pass_kernel<P, IPT><<<grid, threads, smem, s>>>(p);
+    pass_kernel<P, IPT, FUSED><<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <class P, int IPT>
+template <class P, int IPT, bool FUSED>
 inline cudaError_t occupancy_pass(int threads, size_t ring_bytes, int *blocks) {
     const size_t smem = pass_smem<P, IPT>(ring_bytes, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) {
         *blocks = 0;
         return cudaSuccess;
     }
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT>, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT, FUSED>, threads, smem);
 }
 
-template <class P>
-inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t smem,
-                                cudaStream_t s, int *blocks) {
+template <class P, bool FUSED>
+inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t smem,
+                                  cudaStream_t s, int *blocks) {
     switch (ipt) {
-        case 1: return occ ? occupancy_pass<P, 1>(threads, smem, blocks) : launch_pass<P, 1>(*p, grid, threads, smem, s);
-        case 2: return occ ? occupancy_pass<P, 2>(threads, smem, blocks) : launch_pass<P, 2>(*p, grid, threads, smem, s);
-        case 4: return occ ? occupancy_pass<P, 4>(threads, smem, blocks) : launch_pass<P, 4>(*p, grid, threads, smem, s);
+        case 1: return occ ? occupancy_pass<P, 1, FUSED>(threads, smem, blocks) : launch_pass<P, 1, FUSED>(*p, grid, threads, smem, s);
+        case 2: return occ ? occupancy_pass<P, 2, FUSED>(threads, smem, blocks) : launch_pass<P, 2, FUSED>(*p, grid, threads, smem, s);
+        case 4: return occ ? occupancy_pass<P, 4, FUSED>(threads, smem, blocks) : launch_pass<P, 4, FUSED>(*p, grid, threads, smem, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// fused = 1 is available for the mixed force policies only
+template <class P>
+inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t smem,
+                                cudaStream_t s, int *blocks, int fused = 0) {
+    if constexpr (P::kCanFuse) {
+        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, smem, s, blocks);
+    } else {
+        if (fused) return cudaErrorInvalidValue;
+    }
+    return dispatch_ipt_f<P, false>(occ, ipt, p, grid, threads, smem, s, blocks);
 }
 
 template <class P>
 inline cudaError_t launch_reduce(const ReduceParams &r, cudaStream_t s) {
     const int threads = 256;
-    if (r.split >= 32) {
+    if (r.split >= kWarpReduceMinSplit && r.n_i <= kBlockReduceMaxSinks) {
+        reduce_block_kernel<P><<<static_cast<unsigned>(r.n_i), 256, 0, s>>>(r);
+    } else if (r.split >= kWarpReduceMinSplit) {
         const int64_t grid = (32 * r.n_i + threads - 1) / threads;
         reduce_warp_kernel<P><<<static_cast<unsigned>(grid), threads, 0, s>>>(r);
     } else {
@@ -961,12 +1097,16 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
     namespace sp2 {                                                                                        \
     cudaError_t launch_force_##SUFFIX(const KernelKey &k, const ForceParams &p, int grid, int threads,     \
                                       size_t smem, cudaStream_t s) {                                       \
-        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, smem, s, nullptr)  \
-                    : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, smem, s, nullptr);\
+        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, smem, s, nullptr,  \
+                                                        k.fused)                                           \
+                    : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, smem, s, nullptr, \
+                                                         k.fused);                                         \
     }                                                                                                      \
     cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t smem, int *blocks) {       \
-        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks)  \
-                    : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks);\
+        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks,  \
+                                                        k.fused)                                           \
+                    : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks, \
+                                                         k.fused);                                         \
     }                                                                                                      \
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {        \
         return k.nn ? launch_reduce<POLICY<ORDER, true>>(r, s) : launch_reduce<POLICY<ORDER, false>>(r, s); \

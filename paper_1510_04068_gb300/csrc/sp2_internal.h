@@ -59,19 +59,30 @@ struct ForceParams {
     double *acc, *jerk, *snap, *pot;
     int32_t *nn_id;
     double *nn_r2;
-    // partial results (split > 1): part[f * split * n_i + slice * n_i + i]
+    // partial results (split > 1), NF = summed fields (+1 for the NN r^2):
+    //   field-major (sink_major = 0): part[f * split * n_i + slice * n_i + i],
+    //                                 part_id[slice * n_i + i]
+    //   sink-major  (sink_major = 1): part[(i * NF + f) * split + slice],
+    //                                 part_id[i * split + slice]
+    // sink-major is used with the warp-per-sink reduction (split >= 32), so a
+    // warp reads its sink's slices contiguously.
     double *part;
-    int32_t *part_id;          // [slice * n_i + i]
+    int32_t *part_id;
+    int sink_major;
     // VJP outputs / flags
     double *xbar, *vbar, *mbar;
     int accumulate;
+    // fused prediction (mixed policies): sources and sinks are predicted from
+    // the double-single cache to t = t_hi + t_lo inside the pass
+    const float4 *dsc;
+    float t_hi, t_lo;
 };
 
 struct ReduceParams {
     const double *part;
     const int32_t *part_id;
     int64_t n_i;
-    int split;
+    int split;                 // >= 32: warp per sink on the sink-major layout
     double *acc, *jerk, *snap, *pot;
     int32_t *nn_id;
     double *nn_r2;
@@ -93,12 +104,19 @@ struct BatchParams {
 
 enum Kind { K_FORCE = 0, K_VJP = 1 };
 
+// From this many slices on, the split-j reduction runs one warp per sink on
+// the sink-major partial layout (ForceParams::sink_major).
+constexpr int kWarpReduceMinSplit = 32;
+// Up to this many sinks, that reduction uses a whole block per sink.
+constexpr int64_t kBlockReduceMaxSinks = 1024;
+
 struct KernelKey {
     int kind;   // K_FORCE / K_VJP
     int order;  // 4 / 6 (VJP: 4)
     int mixed;  // 0 / 1
     int nn;     // 0 / 1
     int ipt;    // 1 / 2 / 4
+    int fused;  // 1: predict sources in the pass (mixed force only)
 };
 
 // Each kernel translation unit provides these for its (order, precision).

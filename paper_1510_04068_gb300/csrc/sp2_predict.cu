@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sp2_ds.cuh"
 #include "sp2_internal.h"
 
 namespace sp2 {
@@ -23,16 +24,15 @@ inline unsigned grid_for(int64_t n) { return static_cast<unsigned>((n + kThreads
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 
-// Double-single split: hi = fl32(x), lo = fl32(x - hi).
-__device__ __forceinline__ void ds_split(double x, float &hi, float &lo) {
-    hi = __double2float_rn(x);
-    lo = __double2float_rn(x - static_cast<double>(hi));
-}
 
 __device__ __forceinline__ void store_mixed(unsigned char *rec, int rb, int64_t j, const double *xp,
                                             const double *vp, const double *ap, double m, int id) {
     float xh[3], xl[3];
-    for (int c = 0; c < 3; ++c) ds_split(xp[c], xh[c], xl[c]);
+    for (int c = 0; c < 3; ++c) {
+        const ds q = ds_split(xp[c]);  // hi = fl32(x), lo = fl32(x - hi)
+        xh[c] = q.h;
+        xl[c] = q.l;
+    }
     float4 *o = reinterpret_cast<float4 *>(rec + j * rb);
     o[0] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
     o[1] = make_float4(xl[0], xl[1], xl[2], __int_as_float(id));
@@ -51,40 +51,6 @@ __device__ __forceinline__ void store_fp64(unsigned char *rec, int rb, int64_t j
         o[4] = make_double2(ap[0], ap[1]);
         o[5] = make_double2(ap[2], 0.0);
     }
-}
-
-// ---- double-single arithmetic (Dekker 1971; Knuth's TwoSum; TwoProd by FMA).
-// Every step is explicitly rounded so no multiply-add is fused behind our back.
-struct ds {
-    float h, l;
-};
-__device__ __forceinline__ ds two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ ds fast_two_sum(float a, float b) {  // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ds ds_add(ds a, ds b) {
-    ds s = two_sum(a.h, b.h);
-    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ ds ds_add_f(ds a, float b) {
-    ds s = two_sum(a.h, b);
-    return fast_two_sum(s.h, __fadd_rn(s.l, a.l));
-}
-__device__ __forceinline__ ds ds_mul(ds a, ds b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ ds ds_split(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - static_cast<double>(h))};
 }
 
 __device__ __forceinline__ void write_dscache(const JStore &d, int64_t s) {
@@ -111,45 +77,18 @@ __global__ void dscache_kernel(JStore d, int64_t first, int64_t n) {
     if (k < n) write_dscache(d, first + k);
 }
 
-// Mixed-precision predictor on the double-single cache.  Positions:
-//   x_p = x + dt (v + dt (a/2 + dt (j/6 [+ dt s/24])))
-// with x, v, a/2 and dt as double-single values and the jerk / snap terms in
-// FP32 (they enter multiplied by dt^3, far below the double-single
-// resolution of x); velocities and accelerations leave as FP32 values.
+// Mixed-precision predictor on the double-single cache (predict_ds_record).
 template <int ORDER>
 __global__ void predict_ds_kernel(const float4 *dsc, int64_t n, float t_hi, float t_lo, unsigned char *rec) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    constexpr int W = (ORDER == 6) ? 8 : 7;
-    const float4 *q = dsc + j * W;
-    const float4 w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4], w5 = q[5], w6 = q[6];
-    float4 w7 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ORDER == 6) w7 = q[7];
-    const ds dt = ds_add({t_hi, t_lo}, {-w1.w, -w2.w});
-    const float xh[3] = {w0.x, w0.y, w0.z}, xl[3] = {w1.x, w1.y, w1.z};
-    const float vh[3] = {w2.x, w2.y, w2.z}, vl[3] = {w3.x, w3.y, w3.z};
-    const float ah[3] = {w4.x, w4.y, w4.z}, al[3] = {w5.x, w5.y, w5.z};
-    const float jk[3] = {w6.x, w6.y, w6.z}, sn[3] = {w7.x, w7.y, w7.z};
-    float oh[3], ol[3], ov[3], oa[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        // innermost FP32 terms: j/6 (+ dt s/24) for x, j/2 (+ dt s/6) for v, j (+ dt s/2) for a
-        const float jx = (ORDER == 6) ? fmaf(dt.h * (1.f / 24.f), sn[c], jk[c] * (1.f / 6.f)) : jk[c] * (1.f / 6.f);
-        const ds cx = ds_add_f({0.5f * ah[c], 0.5f * al[c]}, dt.h * jx);
-        const ds bx = ds_add({vh[c], vl[c]}, ds_mul(dt, cx));
-        const ds px = ds_add({xh[c], xl[c]}, ds_mul(dt, bx));
-        oh[c] = px.h;
-        ol[c] = px.l;
-        const float jv = (ORDER == 6) ? fmaf(dt.h * (1.f / 6.f), sn[c], 0.5f * jk[c]) : 0.5f * jk[c];
-        ov[c] = vh[c] + fmaf(dt.h, fmaf(dt.h, jv, ah[c] + al[c]), vl[c]);
-        if (ORDER == 6) oa[c] = ah[c] + fmaf(dt.h, fmaf(dt.h, 0.5f * sn[c], jk[c]), al[c]);
-    }
-    const int rb = (ORDER == 6) ? 64 : 48;
-    float4 *o = reinterpret_cast<float4 *>(rec + j * rb);
-    o[0] = make_float4(oh[0], oh[1], oh[2], w0.w);
-    o[1] = make_float4(ol[0], ol[1], ol[2], w3.w);
-    o[2] = make_float4(ov[0], ov[1], ov[2], 0.f);
-    if (ORDER == 6) o[3] = make_float4(oa[0], oa[1], oa[2], 0.f);
+    float4 o[4];
+    predict_ds_record<ORDER>(dsc, j, t_hi, t_lo, o);
+    float4 *dst = reinterpret_cast<float4 *>(rec + j * (ORDER == 6 ? 64 : 48));
+    dst[0] = o[0];
+    dst[1] = o[1];
+    dst[2] = o[2];
+    if (ORDER == 6) dst[3] = o[3];
 }
 
 __global__ void scatter_kernel(JStore d, const int32_t *slots, int64_t n, int64_t n_loaded, unsigned int *err,
@@ -266,7 +205,11 @@ __device__ __forceinline__ void store_vjp(bool mixed, unsigned char *rec, int64_
                                           const double *ab, const double *jb, double pb, double m) {
     if (mixed) {
         float xh[3], xl[3];
-        for (int c = 0; c < 3; ++c) ds_split(xp[c], xh[c], xl[c]);
+        for (int c = 0; c < 3; ++c) {
+        const ds q = ds_split(xp[c]);  // hi = fl32(x), lo = fl32(x - hi)
+        xh[c] = q.h;
+        xl[c] = q.l;
+    }
         float4 *o = reinterpret_cast<float4 *>(rec + j * 80);
         o[0] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
         o[1] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(pb));

@@ -155,6 +155,7 @@ extern "C" sp2_status sp2_step_static(int64_t n_j, const int32_t *id, const doub
     int32_t *part_id = reinterpret_cast<int32_t *>(part_base + static_cast<size_t>(split) * n_i * (kFields + nn) * sizeof(double));
     fp.part = part;
     fp.part_id = part_id;
+    fp.sink_major = split >= kWarpReduceMinSplit ? 1 : 0;
     const int grid = static_cast<int>(std::min<int64_t>(fp.n_items, static_cast<int64_t>(sms) * per_sm));
     if (launch_force_kernel(key, fp, grid, L.threads, smem, s) != cudaSuccess) return SP2_ERR_CUDA;
     if (split > 1) {

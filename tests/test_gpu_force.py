@@ -143,3 +143,46 @@ def test_empty_sink_list_is_a_noop(sp2):
         c.compute(torch.empty(0, dtype=torch.int32, device="cuda"))
         c.sync()
         assert c.kernel_launches() == before
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_fused_prediction_small_n_active(sp2, oracle_mod, order):
+    """Mixed precision with few sinks: the force pass predicts its sources from
+    the double-single cache (no predictor launch); a shape with several
+    i-blocks writes the records first.  Both match the oracle, and a later
+    consumer of the records (a large sink list) sees the same predicted state."""
+    import torch
+    n, eps2 = 6000, 1e-8
+    s = state(n, 70 + order, order=order)
+    D = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    with sp2.Context(order=order, precision=sp2.SP2_MIXED, n_max=n, eps2=eps2, profile=1) as c:
+        c.set_j(0, D(s["ids"]), D(s["m"]), D(s["x"]), D(s["v"]), D(s["a"]), D(s["jerk"]),
+                D(s["snap"]) if order == 6 else None, D(s["tj"]))
+        for n_i, shape, fused in ((1, dict(threads=32, i_per_thread=1, j_lanes=32, j_tile=256, split_j=40), True),
+                                  (37, dict(threads=128, i_per_thread=1, j_lanes=2, j_tile=128, split_j=20), True),
+                                  (37, dict(threads=32, i_per_thread=1, j_lanes=1, j_tile=64, split_j=20), False),
+                                  (300, dict(threads=256, i_per_thread=2, j_lanes=1, j_tile=128, split_j=9), True)):
+            idx = np.sort(np.random.default_rng(n_i).choice(n, n_i, replace=False)).astype(np.int32)
+            c.predict(s["t"])
+            c.set_launch(n_i, dict(shape, ctas_per_sm=0))
+            c.profile_reset()
+            out = dict(acc=torch.empty((n_i, 3), dtype=torch.float64, device="cuda"),
+                       jerk=torch.empty((n_i, 3), dtype=torch.float64, device="cuda"),
+                       snap=torch.empty((n_i, 3), dtype=torch.float64, device="cuda") if order == 6 else None,
+                       pot=torch.empty(n_i, dtype=torch.float64, device="cuda"),
+                       nn_id=torch.empty(n_i, dtype=torch.int32, device="cuda"),
+                       nn_r2=torch.empty(n_i, dtype=torch.float64, device="cuda"))
+            c.compute(D(idx), **out)
+            prof = c.profile_read()
+            assert (prof["predict"][0] == 0) == fused, (n_i, shape, prof)
+            g = {k: (None if v is None else v.cpu().numpy()) for k, v in out.items()}
+            r = oracle_ref(oracle_mod, s, idx, order=order, eps2=eps2)
+            check(g, r, order=order, mixed=True, s=s, i_idx=idx, label=f"fused={fused} n_i={n_i}")
+        # records written on demand for a consumer that needs them
+        idx = np.arange(0, n, 2, dtype=np.int32)
+        acc = torch.empty((len(idx), 3), dtype=torch.float64, device="cuda")
+        pot = torch.empty(len(idx), dtype=torch.float64, device="cuda")
+        c.compute(D(idx), acc=acc, pot=pot)
+        r = oracle_ref(oracle_mod, s, idx, order=order, eps2=eps2)
+        e = np.linalg.norm(acc.cpu().numpy() - r["acc"], axis=1) / r["sc_acc"]
+        assert e.max() <= 1e-6
