@@ -243,6 +243,17 @@ struct PassOut {
     int accumulate = 0;
 };
 
+// Dynamic shared memory of a pass launch (the kernel side computes the same):
+// the kStages-deep record ring, for the mixed force passes one more tile of
+// pair records, and for the mixed policies the FP64 totals of every
+// (thread, sink, field).
+size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt) {
+    const size_t ring = static_cast<size_t>(kStagesDevice) * tile * rb;
+    const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
+    const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
+    return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);
+}
+
 // rec holds n_valid records; sink slots must lie in [0, n_valid).  With
 // allow_fused (the context's own records, mixed precision) a launch whose sinks
 // fit one i-block predicts its sources from the double-single cache inside the
@@ -273,7 +284,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     split = ceil_div(n_j, slice_len);
     const size_t smem = static_cast<size_t>(kStagesDevice) * tile * rb;
     const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
-    const size_t smem_total = smem + (mixed ? static_cast<size_t>(L.threads) * L.i_per_thread * ns_fields * 8 : 0);
+    const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread);
     if (smem_total > 200 * 1024)
         return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max 200 KiB)", smem_total);
     if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
@@ -1009,9 +1020,9 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     auto occupancy = [&](const sp2_launch &L) -> int {
         int occ = 0;
         const size_t ring = static_cast<size_t>(kStagesDevice) * L.j_tile * c->rb;
-        const size_t tot = mixed ? static_cast<size_t>(L.threads) * L.i_per_thread * (order == 6 ? 10 : 7) * 8 : 0;
         KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread};
-        if (ring + tot > 200 * 1024 || force_kernel_occupancy(key, L.threads, ring, &occ) != cudaSuccess) {
+        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread) > 200 * 1024 ||
+            force_kernel_occupancy(key, L.threads, ring, &occ) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }

@@ -47,6 +47,47 @@ __device__ __forceinline__ uint4 d2bits(double a, double b) {
                       static_cast<unsigned>(y >> 32));
 }
 
+// Packed FP32 pairs (f32x2): one instruction performs the same IEEE operation
+// on both halves, each rounded as the scalar instruction would be.  The FMA
+// pipe's lane throughput is unchanged, but a pair costs one issue slot, which
+// leaves the others to the SFU, integer and shared-memory instructions.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.ftz.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.ftz.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.ftz.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+// a * b + c with one rounding per half
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%6, %7};\n\tfma.rn.ftz.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// Policies that evaluate two sources per step define kPaired = true.
+template <class P, class = void>
+struct is_paired { static constexpr bool value = false; };
+template <class P>
+struct is_paired<P, decltype(void(P::kPaired))> { static constexpr bool value = P::kPaired; };
+
 // Lexicographic (r2, id) minimum; id -1 means "none" and only pairs with r2 = +inf.
 __device__ __forceinline__ void nn_merge(double &d, int &id, double od, int oid) {
     if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) {
@@ -268,6 +309,194 @@ struct MixedForce {
         if (NN) {
             if (o.nn_id) o.nn_id[i] = id;
             if (o.nn_r2) o.nn_r2[i] = (id < 0) ? d_inf() : d;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The mixed force policy evaluated two sources at a time in packed FP32 pairs
+// (f32x2): half .x of every pair belongs to the first source of the pair,
+// half .y to the second.  The pass kernel re-lays each staged tile as pair
+// records (PRB bytes): natural word w = {e0,e1,e2,e3} of sources a and b
+// becomes the two words {e0a,e0b,e1a,e1b} and {e2a,e2b,e3a,e3b}, so every
+// operand pair is an aligned register pair straight from shared memory.  The
+// sink's values are held duplicated in both halves.  Each half keeps its own
+// two-level partial sums; the halves are added when the second level is
+// flushed to FP64.  The arithmetic of each half is that of
+// MixedForce::interact, operation for operation.
+// ---------------------------------------------------------------------------
+template <int ORDER, bool NN>
+struct MixedPairForce : MixedForce<ORDER, NN> {
+    typedef MixedForce<ORDER, NN> Base;
+    using Base::NS;
+    using Base::kKeyMask;
+    using typename Base::Rec;
+    static constexpr bool kPaired = true;
+    static constexpr int PRB = 2 * Base::RB;  // bytes of one pair record
+    struct PRec {
+        float4 w0, w1, w2, w4, w6;  // {xh,yh}, {zh,m}, {xl,yl}, {vx,vy}, [{ax,ay}]
+        float2 w3, w5, w7;          // {zl}, {vz}, [{az}]
+    };
+    __device__ static __forceinline__ PRec ld_pair(const unsigned char *q) {
+        const float4 *w = reinterpret_cast<const float4 *>(q);
+        PRec r;
+        r.w0 = w[0]; r.w1 = w[1]; r.w2 = w[2];
+        r.w3 = *reinterpret_cast<const float2 *>(w + 3);
+        r.w4 = w[4];
+        r.w5 = *reinterpret_cast<const float2 *>(w + 5);
+        if (ORDER == 6) {
+            r.w6 = w[6];
+            r.w7 = *reinterpret_cast<const float2 *>(w + 7);
+        }
+        return r;
+    }
+    // words 2w and 2w+1 of the pair record q from natural word w of sources a (x) and b (y)
+    __device__ static __forceinline__ void store_pair_word(const float4 &x, const float4 &y, int w, unsigned char *q) {
+        float4 *d = reinterpret_cast<float4 *>(q) + 2 * w;
+        d[0] = make_float4(x.x, y.x, x.y, y.y);
+        d[1] = make_float4(x.z, y.z, x.w, y.w);
+    }
+    __device__ static __forceinline__ void pack_word(const unsigned char *a, const unsigned char *b, int w,
+                                                     unsigned char *q) {
+        store_pair_word(reinterpret_cast<const float4 *>(a)[w], reinterpret_cast<const float4 *>(b)[w], w, q);
+    }
+    struct Sink {
+        float2 xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;
+        int slot;
+    };
+    struct Acc {
+        float2 f[NS];
+        float2 g[NS];
+        unsigned ck, bk;
+        int bbase;
+    };
+    __device__ static __forceinline__ void sink_from(const Rec &r, Sink &s) {
+        s.xh = dup2(r.w[0].x); s.yh = dup2(r.w[0].y); s.zh = dup2(r.w[0].z);
+        s.xl = dup2(r.w[1].x); s.yl = dup2(r.w[1].y); s.zl = dup2(r.w[1].z);
+        s.vx = dup2(r.w[2].x); s.vy = dup2(r.w[2].y); s.vz = dup2(r.w[2].z);
+        if (ORDER == 6) { s.ax = dup2(r.w[3].x); s.ay = dup2(r.w[3].y); s.az = dup2(r.w[3].z); }
+        else { s.ax = s.ay = s.az = dup2(0.f); }
+    }
+    __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
+        sink_from(Base::ld_global(rec + slot * Base::RB), s);
+    }
+    __device__ static __forceinline__ void init(Acc &c) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = dup2(0.f);
+        c.ck = c.bk = 0xffffffffu;
+        c.bbase = -1;
+    }
+    __device__ static __forceinline__ float dist2(const Rec &r, const Sink &s) {
+        const float dx = (r.w[0].x - s.xh.x) + (r.w[1].x - s.xl.x);
+        const float dy = (r.w[0].y - s.yh.x) + (r.w[1].y - s.yl.x);
+        const float dz = (r.w[0].z - s.zh.x) + (r.w[1].z - s.zl.x);
+        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    }
+    // Sources a (slot j, chunk position u) and b (slot j + jl, position u + 1).
+    template <bool SELF, bool FIRST>
+    __device__ static __forceinline__ void interact2(const PRec &r, int j, int jl, int u, const Sink &s, Acc &c,
+                                                     float eps2) {
+        const float2 dx = add2(sub2(make_float2(r.w0.x, r.w0.y), s.xh), sub2(make_float2(r.w2.x, r.w2.y), s.xl));
+        const float2 dy = add2(sub2(make_float2(r.w0.z, r.w0.w), s.yh), sub2(make_float2(r.w2.z, r.w2.w), s.yl));
+        const float2 dz = add2(sub2(make_float2(r.w1.x, r.w1.y), s.zh), sub2(r.w3, s.zl));
+        const float2 dvx = sub2(make_float2(r.w4.x, r.w4.y), s.vx);
+        const float2 dvy = sub2(make_float2(r.w4.z, r.w4.w), s.vy);
+        const float2 dvz = sub2(r.w5, s.vz);
+        const float2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float2 d2e = add2(d2, dup2(eps2));
+        float2 rinv = make_float2(rsqrtf(d2e.x), rsqrtf(d2e.y));
+        if (SELF) {
+            if (j == s.slot) rinv.x = 0.f;
+            if (j + jl == s.slot) rinv.y = 0.f;
+        }
+        const float2 rinv2 = mul2(rinv, rinv);
+        const float2 mr = mul2(make_float2(r.w1.z, r.w1.w), rinv);
+        const float2 mr3 = mul2(mr, rinv2);
+        c.f[NS - 1] = FIRST ? mr : add2(c.f[NS - 1], mr);
+        const float2 rv = fma2(dz, dvz, fma2(dy, dvy, mul2(dx, dvx)));
+        const float2 al = mul2(rv, rinv2);
+        const float2 nal3 = mul2(dup2(-3.f), al);  // -alpha * 3 (sign folded into the constant)
+        if (ORDER == 4) {
+            c.f[0] = FIRST ? mul2(mr3, dx) : fma2(mr3, dx, c.f[0]);
+            c.f[1] = FIRST ? mul2(mr3, dy) : fma2(mr3, dy, c.f[1]);
+            c.f[2] = FIRST ? mul2(mr3, dz) : fma2(mr3, dz, c.f[2]);
+            c.f[3] = FIRST ? mul2(mr3, fma2(nal3, dx, dvx)) : fma2(mr3, fma2(nal3, dx, dvx), c.f[3]);
+            c.f[4] = FIRST ? mul2(mr3, fma2(nal3, dy, dvy)) : fma2(mr3, fma2(nal3, dy, dvy), c.f[4]);
+            c.f[5] = FIRST ? mul2(mr3, fma2(nal3, dz, dvz)) : fma2(mr3, fma2(nal3, dz, dvz), c.f[5]);
+        } else {
+            const float2 dax = sub2(make_float2(r.w6.x, r.w6.y), s.ax);
+            const float2 day = sub2(make_float2(r.w6.z, r.w6.w), s.ay);
+            const float2 daz = sub2(r.w7, s.az);
+            const float2 Ax = mul2(mr3, dx), Ay = mul2(mr3, dy), Az = mul2(mr3, dz);
+            const float2 Jx = fma2(nal3, Ax, mul2(mr3, dvx));
+            const float2 Jy = fma2(nal3, Ay, mul2(mr3, dvy));
+            const float2 Jz = fma2(nal3, Az, mul2(mr3, dvz));
+            const float2 vv = fma2(dvz, dvz, fma2(dvy, dvy, mul2(dvx, dvx)));
+            const float2 ra = fma2(dz, daz, fma2(dy, day, mul2(dx, dax)));
+            const float2 nb3 = mul2(dup2(-3.f), fma2(add2(vv, ra), rinv2, mul2(al, al)));
+            const float2 na6 = mul2(dup2(2.f), nal3);
+            const float2 Sx = fma2(mr3, dax, fma2(na6, Jx, mul2(nb3, Ax)));
+            const float2 Sy = fma2(mr3, day, fma2(na6, Jy, mul2(nb3, Ay)));
+            const float2 Sz = fma2(mr3, daz, fma2(na6, Jz, mul2(nb3, Az)));
+            if (FIRST) {
+                c.f[0] = Ax; c.f[1] = Ay; c.f[2] = Az;
+                c.f[3] = Jx; c.f[4] = Jy; c.f[5] = Jz;
+                c.f[6] = Sx; c.f[7] = Sy; c.f[8] = Sz;
+            } else {
+                c.f[0] = add2(c.f[0], Ax); c.f[1] = add2(c.f[1], Ay); c.f[2] = add2(c.f[2], Az);
+                c.f[3] = add2(c.f[3], Jx); c.f[4] = add2(c.f[4], Jy); c.f[5] = add2(c.f[5], Jz);
+                c.f[6] = add2(c.f[6], Sx); c.f[7] = add2(c.f[7], Sy); c.f[8] = add2(c.f[8], Sz);
+            }
+        }
+        if (NN) {
+            const unsigned ka = (SELF && j == s.slot) ? 0xffffffffu : ((__float_as_uint(d2.x) & ~kKeyMask) | unsigned(u));
+            const unsigned kb =
+                (SELF && j + jl == s.slot) ? 0xffffffffu : ((__float_as_uint(d2.y) & ~kKeyMask) | unsigned(u + 1));
+            c.ck = FIRST ? min(ka, kb) : min(c.ck, min(ka, kb));
+        }
+    }
+    __device__ static __forceinline__ void fold(Acc &c, int base) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.g[f] = add2(c.g[f], c.f[f]);
+        if (NN && c.ck < c.bk) {
+            c.bk = c.ck;
+            c.bbase = base;
+        }
+    }
+    // level 2 (both halves) -> FP64 totals tot[f * stride]
+    __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) {
+            tot[f * stride] += static_cast<double>(c.g[f].x) + static_cast<double>(c.g[f].y);
+            c.g[f] = dup2(0.f);
+        }
+    }
+    __device__ static __forceinline__ void totals(const Acc &, const double *tot, int stride, double *t) {
+        Base::totals(typename Base::Acc{}, tot, stride, t);
+    }
+    __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
+                                              int jl, double &d, int &id) {
+        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
+        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
+            const Rec r = Base::ld_global(rec + j * Base::RB);
+            d = static_cast<double>(dist2(r, s));
+            id = __float_as_int(r.w[1].w);
+        } else {
+            d = d_inf();
+            id = -1;
+        }
+    }
+    template <bool FUSED>
+    __device__ static __forceinline__ void nn_lookup(const Acc &c, const Sink &s, const ForceParams &p, int64_t limit,
+                                                     int jl, double &d, int &id) {
+        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
+        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
+            const Rec r = FUSED ? Base::predict(p.dsc, j, p.t_hi, p.t_lo) : Base::ld_global(p.rec + j * Base::RB);
+            d = static_cast<double>(dist2(r, s));
+            id = __float_as_int(r.w[1].w);
+        } else {
+            d = d_inf();
+            id = -1;
         }
     }
 };
@@ -627,7 +856,33 @@ __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *s
     const int64_t rem = j1 - tb;
     const int cnt = rem < tile ? static_cast<int>(rem) : tile;
     constexpr int W = P::RB / 16;
-    if constexpr (FUSED && P::kCanFuse) {
+    if constexpr (FUSED && P::kCanFuse && is_paired<P>::value) {
+        // predict the tile's sources from the double-single cache (one per
+        // thread) straight into pair records: source c = lj + jl*m is half
+        // m & 1 of pair (m >> 1) * jl + lj
+        const int jl = p.jl;
+        for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+            const int lj = c & (jl - 1), m = c / jl;
+            float *q = reinterpret_cast<float *>(dst + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
+            typename P::Rec r;
+            if (c < cnt) {
+                r = P::predict(p.dsc, tb + c, p.t_hi, p.t_lo);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const uint4 u = P::sentinel(w);
+                    r.w[w] = *reinterpret_cast<const float4 *>(&u);
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                q[8 * w] = r.w[w].x;
+                q[8 * w + 2] = r.w[w].y;
+                q[8 * w + 4] = r.w[w].z;
+                q[8 * w + 6] = r.w[w].w;
+            }
+        }
+    } else if constexpr (FUSED && P::kCanFuse) {
         // predict the tile's sources from the double-single cache (one per thread)
         for (int c = threadIdx.x; c < tile; c += blockDim.x) {
             uint4 *d = reinterpret_cast<uint4 *>(dst + static_cast<size_t>(c) * P::RB);
@@ -650,32 +905,72 @@ __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *s
     }
 }
 
+// Re-lay a staged tile of natural records as pair records: lane lj's sources
+// m = 2k and 2k+1 (tile positions lj + jl*m) form pair k*jl + lj.
+template <class P>
+__device__ __forceinline__ void pair_tile(const unsigned char *st, unsigned char *q, int tile, int jl) {
+    constexpr int W = P::RB / 16;
+    const int items = (tile >> 1) * W;
+    for (int i = threadIdx.x; i < items; i += blockDim.x) {
+        const int pr = i / W, w = i - pr * W;
+        const int k = pr / jl, lj = pr - k * jl;
+        const int a = lj + 2 * k * jl;
+        P::pack_word(st + a * P::RB, st + (a + jl) * P::RB, w, q + pr * P::PRB);
+    }
+}
+
 template <class P, int IPT, bool SELF>
 __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int per, int jl, int lj,
                                           const typename P::Sink *sk, typename P::Acc *ac,
                                           typename P::real eps2) {
     const unsigned char *base = st + lj * P::RB;
     const int step = jl * P::RB;
-    for (int q0 = 0; q0 < per; q0 += P::kChunk) {
-        const int jb = tb + q0 * jl + lj;  // this thread's first source of the chunk
-        {
-            const typename P::Rec r = P::ld_shared(base + q0 * step);
+    if constexpr (is_paired<P>::value) {
+        // st holds pair records: lane lj's k-th pair (its sources 2k and 2k+1)
+        // sits at pair index k * jl + lj.
+        const unsigned char *pbase = st + lj * P::PRB;
+        const int pstep = jl * P::PRB;
+        for (int q0 = 0; q0 < per; q0 += P::kChunk) {
+            const int jb = tb + q0 * jl + lj;
+            const unsigned char *pq = pbase + (q0 >> 1) * pstep;
+            {
+                const typename P::PRec r = P::ld_pair(pq);
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) P::template interact<SELF, true>(r, jb, 0, sk[k], ac[k], eps2);
+                for (int k = 0; k < IPT; ++k) P::template interact2<SELF, true>(r, jb, jl, 0, sk[k], ac[k], eps2);
+            }
+#pragma unroll
+            for (int u = 2; u < P::kChunk; u += 2) {
+                const typename P::PRec r = P::ld_pair(pq + (u >> 1) * pstep);
+#pragma unroll
+                for (int k = 0; k < IPT; ++k)
+                    P::template interact2<SELF, false>(r, jb + u * jl, jl, u, sk[k], ac[k], eps2);
+            }
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb);
         }
+    } else {
+        for (int q0 = 0; q0 < per; q0 += P::kChunk) {
+            const int jb = tb + q0 * jl + lj;  // this thread's first source of the chunk
+            {
+                const typename P::Rec r = P::ld_shared(base + q0 * step);
 #pragma unroll
-        for (int u = 1; u < P::kChunk; ++u) {
-            const typename P::Rec r = P::ld_shared(base + (q0 + u) * step);
+                for (int k = 0; k < IPT; ++k) P::template interact<SELF, true>(r, jb, 0, sk[k], ac[k], eps2);
+            }
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) P::template interact<SELF, false>(r, jb + u * jl, u, sk[k], ac[k], eps2);
+            for (int u = 1; u < P::kChunk; ++u) {
+                const typename P::Rec r = P::ld_shared(base + (q0 + u) * step);
+#pragma unroll
+                for (int k = 0; k < IPT; ++k) P::template interact<SELF, false>(r, jb + u * jl, u, sk[k], ac[k], eps2);
+            }
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb);
         }
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb);
     }
 }
 
-// Shared memory: kStages tiles of records, then (mixed policies) the FP64
-// totals, [sink k][field f][thread] so each thread owns its slots.
+// Shared memory: kStages tiles of records, (paired policies) one tile of pair
+// records, then (mixed policies) the FP64 totals, [sink k][field f][thread]
+// so each thread owns its slots.
 template <class P, int IPT, bool FUSED>
 __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -688,7 +983,9 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
     const int slots = nt / jl;
     const typename P::real eps2 = static_cast<typename P::real>(p.eps2);
     const int per = p.tile / jl;  // a multiple of P::kChunk (host-checked)
-    double *tot = reinterpret_cast<double *>(smem + static_cast<size_t>(kStages) * p.tile * P::RB) + tid;
+    constexpr bool kPair = is_paired<P>::value;
+    unsigned char *pbuf = smem + static_cast<size_t>(kStages) * p.tile * P::RB;  // pair records (kPair)
+    double *tot = reinterpret_cast<double *>(smem + static_cast<size_t>(kStages + (kPair ? 1 : 0)) * p.tile * P::RB) + tid;
 
     for (;;) {
         __syncthreads();
@@ -735,6 +1032,12 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             if (t + kStages - 1 < n_tiles) load_tile<P, FUSED>(p, smem, t + kStages - 1, j0, j1);
             cp_async_commit();
             const unsigned char *st = smem + static_cast<size_t>(t % kStages) * p.tile * P::RB;
+            if constexpr (kPair && !FUSED) {
+                // every thread has left the previous tile's pair records (barrier above)
+                pair_tile<P>(st, pbuf, p.tile, jl);
+                __syncthreads();
+                st = pbuf;
+            }
             const int tb = static_cast<int>(j0) + t * p.tile;
             const int te = (tb + p.tile < j1) ? tb + p.tile : static_cast<int>(j1);
             bool mine = false;
@@ -921,17 +1224,29 @@ constexpr int kBatchTile = 64;  // sources per warp-private shared-memory tile
 template <class P, bool SELF>
 __device__ __forceinline__ void batch_tile_loop(const unsigned char *st, int tb, int n, const typename P::Sink &sk,
                                                 typename P::Acc &ac, typename P::real eps2) {
-    for (int q0 = 0; q0 < n; q0 += P::kChunk) {
-        {
-            const typename P::Rec r = P::ld_shared(st + q0 * P::RB);
-            P::template interact<SELF, true>(r, tb + q0, 0, sk, ac, eps2);
-        }
+    if constexpr (is_paired<P>::value) {
+        // st holds pair records of sources (2k, 2k+1)
+        for (int q0 = 0; q0 < n; q0 += P::kChunk) {
+            const unsigned char *pq = st + (q0 >> 1) * P::PRB;
+            P::template interact2<SELF, true>(P::ld_pair(pq), tb + q0, 1, 0, sk, ac, eps2);
 #pragma unroll
-        for (int u = 1; u < P::kChunk; ++u) {
-            const typename P::Rec r = P::ld_shared(st + (q0 + u) * P::RB);
-            P::template interact<SELF, false>(r, tb + q0 + u, u, sk, ac, eps2);
+            for (int u = 2; u < P::kChunk; u += 2)
+                P::template interact2<SELF, false>(P::ld_pair(pq + (u >> 1) * P::PRB), tb + q0 + u, 1, u, sk, ac, eps2);
+            P::fold(ac, tb + q0);
         }
-        P::fold(ac, tb + q0);
+    } else {
+        for (int q0 = 0; q0 < n; q0 += P::kChunk) {
+            {
+                const typename P::Rec r = P::ld_shared(st + q0 * P::RB);
+                P::template interact<SELF, true>(r, tb + q0, 0, sk, ac, eps2);
+            }
+#pragma unroll
+            for (int u = 1; u < P::kChunk; ++u) {
+                const typename P::Rec r = P::ld_shared(st + (q0 + u) * P::RB);
+                P::template interact<SELF, false>(r, tb + q0 + u, u, sk, ac, eps2);
+            }
+            P::fold(ac, tb + q0);
+        }
     }
 }
 
@@ -969,11 +1284,22 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
             const int cnt = min(kBatchTile, it.y - t0);
             const int padded = (cnt + P::kChunk - 1) / P::kChunk * P::kChunk;
             __syncwarp();
-            for (int c = lane; c < padded * W; c += 32) {
-                uint4 w4;
-                if (c < cnt * W) w4 = __ldg(reinterpret_cast<const uint4 *>(src + static_cast<int64_t>(t0) * P::RB) + c);
-                else w4 = P::sentinel(c % W);
-                *reinterpret_cast<uint4 *>(wbuf + 16 * c) = w4;
+            const uint4 *tsrc = reinterpret_cast<const uint4 *>(src + static_cast<int64_t>(t0) * P::RB);
+            if constexpr (is_paired<P>::value) {
+                for (int c = lane; c < (padded >> 1) * W; c += 32) {
+                    const int pr = c / W, w = c - pr * W;
+                    const uint4 x = (2 * pr < cnt) ? __ldg(tsrc + 2 * pr * W + w) : P::sentinel(w);
+                    const uint4 y = (2 * pr + 1 < cnt) ? __ldg(tsrc + (2 * pr + 1) * W + w) : P::sentinel(w);
+                    P::store_pair_word(*reinterpret_cast<const float4 *>(&x), *reinterpret_cast<const float4 *>(&y), w,
+                                       wbuf + pr * P::PRB);
+                }
+            } else {
+                for (int c = lane; c < padded * W; c += 32) {
+                    uint4 w4;
+                    if (c < cnt * W) w4 = __ldg(tsrc + c);
+                    else w4 = P::sentinel(c % W);
+                    *reinterpret_cast<uint4 *>(wbuf + 16 * c) = w4;
+                }
             }
             __syncwarp();
             const int tb = it.x + t0;
@@ -1003,7 +1329,8 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // policies, the FP64 totals of every (thread, sink, field).
 template <class P, int IPT>
 inline size_t pass_smem(size_t ring_bytes, int threads) {
-    return ring_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
+    const size_t pair_bytes = is_paired<P>::value ? ring_bytes / kStages : 0;
+    return ring_bytes + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
 }
 
 constexpr int kMaxDynSmem = 200 * 1024;
@@ -1092,8 +1419,9 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
 
 }  // namespace sp2
 
-// Defines the five per-TU entry points for force policy template POLICY<ORDER, NN>.
-#define SP2_DEFINE_FORCE_TU(SUFFIX, POLICY, ORDER)                                                         \
+// Defines the five per-TU entry points: the pass kernel and its reduction use
+// POLICY<ORDER, NN>, the batched kernel BATCH_POLICY<ORDER, NN>.
+#define SP2_DEFINE_FORCE_TU(SUFFIX, POLICY, BATCH_POLICY, ORDER)                                           \
     namespace sp2 {                                                                                        \
     cudaError_t launch_force_##SUFFIX(const KernelKey &k, const ForceParams &p, int grid, int threads,     \
                                       size_t smem, cudaStream_t s) {                                       \
@@ -1113,11 +1441,11 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
     }                                                                                                      \
     cudaError_t launch_batched_##SUFFIX(int nn, const BatchParams &b, int grid, int threads,               \
                                         cudaStream_t s) {                                                  \
-        return nn ? launch_batched<POLICY<ORDER, true>>(b, grid, threads, s)                               \
-                  : launch_batched<POLICY<ORDER, false>>(b, grid, threads, s);                             \
+        return nn ? launch_batched<BATCH_POLICY<ORDER, true>>(b, grid, threads, s)                               \
+                  : launch_batched<BATCH_POLICY<ORDER, false>>(b, grid, threads, s);                             \
     }                                                                                                      \
     cudaError_t occupancy_batched_##SUFFIX(int nn, int threads, int *blocks) {                             \
-        return nn ? occupancy_batched<POLICY<ORDER, true>>(threads, blocks)                                \
-                  : occupancy_batched<POLICY<ORDER, false>>(threads, blocks);                              \
+        return nn ? occupancy_batched<BATCH_POLICY<ORDER, true>>(threads, blocks)                                \
+                  : occupancy_batched<BATCH_POLICY<ORDER, false>>(threads, blocks);                              \
     }                                                                                                      \
     }

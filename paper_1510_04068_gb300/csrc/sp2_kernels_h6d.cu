@@ -3,4 +3,4 @@
 // variants compile in parallel.
 #include "sp2_device.cuh"
 
-SP2_DEFINE_FORCE_TU(h6d, Fp64Force, 6)
+SP2_DEFINE_FORCE_TU(h6d, Fp64Force, Fp64Force, 6)
