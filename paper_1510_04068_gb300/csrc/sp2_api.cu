@@ -23,6 +23,8 @@ namespace {
 enum Stage { ST_PREDICT = 0, ST_FORCE, ST_REDUCE, ST_BATCHED, ST_VJP, ST_OTHER, ST_COUNT };
 constexpr int kEventRing = 4096;
 constexpr int kStagesDevice = 3;  // must equal sp2::kStages of sp2_device.cuh
+// largest (sinks of one i-block) x (slices) reduced inside the pass kernel
+constexpr int64_t kFusedReduceMaxValues = 16384;
 
 }  // namespace
 
@@ -64,6 +66,8 @@ struct sp2_ctx {
     double *part = nullptr;
     int32_t *part_id = nullptr;
     size_t part_cap = 0, part_id_cap = 0;   // bytes
+    unsigned int *done = nullptr;           // per-i-block arrival counters of the fused reduction
+    size_t done_cap = 0;                    // bytes
     unsigned char *stage = nullptr;  // staging for host-pointer calls
     size_t stage_cap = 0;
     std::vector<void *> owned;       // everything allocated (for close)
@@ -329,6 +333,15 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         p.part = c->part;
         p.part_id = c->part_id;
         p.sink_major = split >= kWarpReduceMinSplit ? 1 : 0;
+        // fuse the reduction into the pass when one CTA's share of it is small
+        if (std::min<int64_t>(sinks_per_cta, n_i) * split <= kFusedReduceMaxValues) {
+            const size_t old_cap = c->done_cap;
+            SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->done), &c->done_cap,
+                           static_cast<size_t>(n_iblk) * sizeof(unsigned int), "reduction-counter"));
+            if (c->done_cap != old_cap) SP2_CK(c, cudaMemsetAsync(c->done, 0, c->done_cap, c->stream));
+            p.fused_reduce = 1;
+            p.done = c->done;
+        }
     }
     SP2_CK(c, cudaMemsetAsync(c->dev_words, 0, sizeof(unsigned int), c->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -341,7 +354,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     SP2_CK(c, launch_force_kernel(key, p, grid, L.threads, smem, c->stream));
     ev_end(c, stage_force);
     c->launches += 1;
-    if (split > 1) {
+    if (split > 1 && !p.fused_reduce) {
         ReduceParams r{};
         r.part = c->part;
         r.part_id = c->part_id;

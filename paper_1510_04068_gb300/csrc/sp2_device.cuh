@@ -322,8 +322,8 @@ struct MixedForce {
 // operand pair is an aligned register pair straight from shared memory.  The
 // sink's values are held duplicated in both halves.  Each half keeps its own
 // two-level partial sums; the halves are added when the second level is
-// flushed to FP64.  The arithmetic of each half is that of
-// MixedForce::interact, operation for operation.
+// flushed into the running double-single totals (see flush).  The arithmetic
+// of each half is that of MixedForce::interact, operation for operation.
 // ---------------------------------------------------------------------------
 template <int ORDER, bool NN>
 struct MixedPairForce : MixedForce<ORDER, NN> {
@@ -463,16 +463,36 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
             c.bbase = base;
         }
     }
-    // level 2 (both halves) -> FP64 totals tot[f * stride]
+    // Level 2 (both halves added) -> the running totals, held as unevaluated
+    // FP32 sums hi + lo (double-single) in the 8-byte slots tot[f * stride]:
+    // hi takes the new value by TwoSum (Knuth), whose exact rounding error
+    // goes to lo, so the totals keep ~48 bits without touching the FP64 pipe
+    // (1/64 of the FP32 rate on this GPU) inside the pass.
     __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
+        float2 *t2 = reinterpret_cast<float2 *>(tot);
 #pragma unroll
         for (int f = 0; f < NS; ++f) {
-            tot[f * stride] += static_cast<double>(c.g[f].x) + static_cast<double>(c.g[f].y);
+            const float v = c.g[f].x + c.g[f].y;
+            float2 T = t2[f * stride];
+            const float h = T.x + v;
+            const float bv = h - T.x;
+            const float e = (T.x - (h - bv)) + (v - bv);
+            T.x = h;
+            T.y += e;
+            t2[f * stride] = T;
             c.g[f] = dup2(0.f);
         }
     }
+    __device__ static __forceinline__ void zero_totals(double *tot, int stride) {
+        float2 *t2 = reinterpret_cast<float2 *>(tot);
+#pragma unroll
+        for (int f = 0; f < NS; ++f) t2[f * stride] = dup2(0.f);
+    }
     __device__ static __forceinline__ void totals(const Acc &, const double *tot, int stride, double *t) {
-        Base::totals(typename Base::Acc{}, tot, stride, t);
+        const float2 *t2 = reinterpret_cast<const float2 *>(tot);
+#pragma unroll
+        for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(t2[f * stride].x) + static_cast<double>(t2[f * stride].y);
+        t[NS - 1] = -t[NS - 1];
     }
     __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
                                               int jl, double &d, int &id) {
@@ -968,6 +988,89 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
     }
 }
 
+// Fused split-j reduction of one i-block, run by the last CTA to finish one
+// of its slices.  Partials are read from L2 (__ldcg: written by other SMs in
+// this launch) in slice order, so the result does not depend on which CTA
+// arrives last.  Field-major partials (few slices): a thread per sink.
+// Sink-major partials (many slices): a warp per sink, or the whole CTA per
+// sink when the i-block has fewer sinks than the CTA has warps.
+template <class P>
+__device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
+    __shared__ double s_t[kMaxThreads / 32][P::NS];
+    __shared__ double s_d[kMaxThreads / 32];
+    __shared__ int s_id[kMaxThreads / 32];
+    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int64_t b0 = iblk * p.sinks_per_cta;
+    const int64_t b1 = (b0 + p.sinks_per_cta < p.n_i) ? b0 + p.sinks_per_cta : p.n_i;
+    const int split = p.split;
+    if (!p.sink_major) {
+        const int64_t stride = static_cast<int64_t>(split) * p.n_i;
+        for (int64_t i = b0 + tid; i < b1; i += nt) {
+            double t[P::NS];
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+            double nd = d_inf();
+            int nid = -1;
+            for (int s = 0; s < split; ++s) {
+                const double *base = p.part + static_cast<int64_t>(s) * p.n_i + i;
+#pragma unroll
+                for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(base + f * stride);
+                if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(p.part_id + static_cast<int64_t>(s) * p.n_i + i));
+            }
+            P::write_final(p, i, t, nd, nid);
+        }
+        return;
+    }
+    const bool per_block = (b1 - b0) < nw;
+    const int lanes = per_block ? nt : 32;
+    const int me = per_block ? tid : lane;
+    for (int64_t i = per_block ? b0 : b0 + warp; i < b1; i += per_block ? 1 : nw) {
+        const double *row = p.part + i * NF * split;
+        const int32_t *row_id = p.part_id + i * split;
+        double t[P::NS];
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+        double nd = d_inf();
+        int nid = -1;
+        for (int s = me; s < split; s += lanes) {
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(row + f * split + s);
+            if (P::kNN) nn_merge(nd, nid, __ldcg(row + P::NS * split + s), __ldcg(row_id + s));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+            if (P::kNN) {
+                const double od = __shfl_xor_sync(kFull, nd, off);
+                const int oid = __shfl_xor_sync(kFull, nid, off);
+                nn_merge(nd, nid, od, oid);
+            }
+        }
+        if (!per_block) {
+            if (lane == 0) P::write_final(p, i, t, nd, nid);
+            continue;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) s_t[warp][f] = t[f];
+            s_d[warp] = nd;
+            s_id[warp] = nid;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nw; ++w) {
+#pragma unroll
+                for (int f = 0; f < P::NS; ++f) t[f] += s_t[w][f];
+                if (P::kNN) nn_merge(nd, nid, s_d[w], s_id[w]);
+            }
+            P::write_final(p, i, t, nd, nid);
+        }
+        __syncthreads();
+    }
+}
+
 // Shared memory: kStages tiles of records, (paired policies) one tile of pair
 // records, then (mixed policies) the FP64 totals, [sink k][field f][thread]
 // so each thread owns its slots.
@@ -987,6 +1090,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
     unsigned char *pbuf = smem + static_cast<size_t>(kStages) * p.tile * P::RB;  // pair records (kPair)
     double *tot = reinterpret_cast<double *>(smem + static_cast<size_t>(kStages + (kPair ? 1 : 0)) * p.tile * P::RB) + tid;
 
+    __shared__ int s_last;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(p.queue, 1u);
@@ -1094,6 +1198,17 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
                         p.part_id[static_cast<int64_t>(slice) * p.n_i + ii[k]] = nid;
                     }
                 }
+            }
+        }
+        if (p.split > 1 && p.fused_reduce) {
+            __threadfence();  // this CTA's partials are visible device-wide before it is counted
+            __syncthreads();
+            if (tid == 0) s_last = (atomicAdd(p.done + iblk, 1u) == static_cast<unsigned>(p.split - 1)) ? 1 : 0;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                reduce_iblock<P>(p, iblk);
+                if (tid == 0) p.done[iblk] = 0u;  // ready for the next launch
             }
         }
     }

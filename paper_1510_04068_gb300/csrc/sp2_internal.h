@@ -69,6 +69,11 @@ struct ForceParams {
     double *part;
     int32_t *part_id;
     int sink_major;
+    // fused reduction (split > 1): the last CTA to finish a slice of an
+    // i-block (counted in done[iblk], zero between launches and reset by that
+    // CTA) sums the i-block's partials in slice order and writes the outputs
+    int fused_reduce;
+    unsigned int *done;
     // VJP outputs / flags
     double *xbar, *vbar, *mbar;
     int accumulate;
