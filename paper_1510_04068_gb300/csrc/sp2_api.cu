@@ -248,11 +248,12 @@ struct PassOut {
 };
 
 // Dynamic shared memory of a pass launch (the kernel side computes the same):
-// the kStages-deep record ring, for the mixed force passes one more tile of
+// the kStages-deep staging ring (records, or double-single cache words when
+// the prediction is fused), for the mixed force passes one more tile of
 // pair records, and for the mixed policies the FP64 totals of every
 // (thread, sink, field).
-size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt) {
-    const size_t ring = static_cast<size_t>(kStagesDevice) * tile * rb;
+size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
+    const size_t ring = static_cast<size_t>(kStagesDevice) * tile * (fused ? dscache_words(order) * 16 : rb);
     const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
     const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
     return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);
@@ -286,9 +287,11 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
-    const size_t smem = static_cast<size_t>(kStagesDevice) * tile * rb;
+    // the staging ring holds predicted records, or with fused prediction the
+    // double-single cache words of the sources
+    const size_t smem = static_cast<size_t>(kStagesDevice) * tile * (fused ? dscache_words(order) * 16 : rb);
     const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
-    const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread);
+    const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused);
     if (smem_total > 200 * 1024)
         return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max 200 KiB)", smem_total);
     if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
@@ -1032,9 +1035,11 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     // resident CTAs per SM of a shape (0 if it does not fit)
     auto occupancy = [&](const sp2_launch &L) -> int {
         int occ = 0;
-        const size_t ring = static_cast<size_t>(kStagesDevice) * L.j_tile * c->rb;
-        KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread};
-        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread) > 200 * 1024 ||
+        // the kernel run_pass will launch: fused prediction when the sinks fit one i-block
+        const int fused = (mixed && c->js.dsc && n_i <= int64_t(L.threads / L.j_lanes) * L.i_per_thread) ? 1 : 0;
+        const size_t ring = static_cast<size_t>(kStagesDevice) * L.j_tile * (fused ? dscache_words(order) * 16 : c->rb);
+        KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread, fused};
+        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, fused) > 200 * 1024 ||
             force_kernel_occupancy(key, L.threads, ring, &occ) != cudaSuccess) {
             cudaGetLastError();
             return 0;

@@ -272,22 +272,8 @@ struct MixedForce {
         t[NS - 1] = -t[NS - 1];
     }
     // The chosen source is slot bbase + u * jl; its r^2 is recomputed exactly
-    // from its record (read, or predicted again when fused).  limit: one past
-    // the last real source slot (filler records never qualify, the bound keeps
-    // the lookup inside the arrays regardless).
-    template <bool FUSED>
-    __device__ static __forceinline__ void nn_lookup(const Acc &c, const Sink &s, const ForceParams &p, int64_t limit,
-                                                     int jl, double &d, int &id) {
-        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
-        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
-            const Rec r = FUSED ? predict(p.dsc, j, p.t_hi, p.t_lo) : ld_global(p.rec + j * RB);
-            d = static_cast<double>(dist2(r, s));
-            id = __float_as_int(r.w[1].w);
-        } else {
-            d = d_inf();
-            id = -1;
-        }
-    }
+    // from its record.  limit: one past the last real source slot (filler
+    // records never qualify, the bound keeps the lookup inside the arrays).
     __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
                                               int jl, double &d, int &id) {
         const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
@@ -369,6 +355,8 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
         float2 g[NS];
         unsigned ck, bk;
         int bbase;
+        float bd;  // nearest neighbour so far: exact r^2 and id (-1: none)
+        int bid;
     };
     __device__ static __forceinline__ void sink_from(const Rec &r, Sink &s) {
         s.xh = dup2(r.w[0].x); s.yh = dup2(r.w[0].y); s.zh = dup2(r.w[0].z);
@@ -385,6 +373,8 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
         for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = dup2(0.f);
         c.ck = c.bk = 0xffffffffu;
         c.bbase = -1;
+        c.bd = f_inf();
+        c.bid = -1;
     }
     __device__ static __forceinline__ float dist2(const Rec &r, const Sink &s) {
         const float dx = (r.w[0].x - s.xh.x) + (r.w[1].x - s.xl.x);
@@ -455,12 +445,30 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
             c.ck = FIRST ? min(ka, kb) : min(c.ck, min(ka, kb));
         }
     }
-    __device__ static __forceinline__ void fold(Acc &c, int base) {
+    // End of a chunk whose pair records start at pq (pair stride pstep).  When
+    // the chunk holds a new nearest neighbour, its exact r^2 (the operations
+    // of interact2 on that half) and id are taken from the chunk's pair record
+    // while it is still in shared memory; filler records (r^2 = inf) never
+    // qualify.
+    __device__ static __forceinline__ void fold(Acc &c, int base, const unsigned char *pq, int pstep, const Sink &s) {
 #pragma unroll
         for (int f = 0; f < NS; ++f) c.g[f] = add2(c.g[f], c.f[f]);
         if (NN && c.ck < c.bk) {
             c.bk = c.ck;
             c.bbase = base;
+            if ((c.ck & ~kKeyMask) < 0x7f800000u) {
+                const int u = static_cast<int>(c.ck & kKeyMask), h = u & 1;
+                // floats of a pair record: xh 0,1  yh 2,3  zh 4,5  xl 8,9  yl 10,11  zl 12,13  id 14,15
+                const float *q = reinterpret_cast<const float *>(pq + (u >> 1) * pstep);
+                const float dx = (q[h] - s.xh.x) + (q[8 + h] - s.xl.x);
+                const float dy = (q[2 + h] - s.yh.x) + (q[10 + h] - s.yl.x);
+                const float dz = (q[4 + h] - s.zh.x) + (q[12 + h] - s.zl.x);
+                c.bd = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                c.bid = __float_as_int(q[14 + h]);
+            } else {
+                c.bd = f_inf();
+                c.bid = -1;
+            }
         }
     }
     // Level 2 (both halves added) -> the running totals, held as unevaluated
@@ -493,31 +501,6 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
 #pragma unroll
         for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(t2[f * stride].x) + static_cast<double>(t2[f * stride].y);
         t[NS - 1] = -t[NS - 1];
-    }
-    __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
-                                              int jl, double &d, int &id) {
-        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
-        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
-            const Rec r = Base::ld_global(rec + j * Base::RB);
-            d = static_cast<double>(dist2(r, s));
-            id = __float_as_int(r.w[1].w);
-        } else {
-            d = d_inf();
-            id = -1;
-        }
-    }
-    template <bool FUSED>
-    __device__ static __forceinline__ void nn_lookup(const Acc &c, const Sink &s, const ForceParams &p, int64_t limit,
-                                                     int jl, double &d, int &id) {
-        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
-        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
-            const Rec r = FUSED ? Base::predict(p.dsc, j, p.t_hi, p.t_lo) : Base::ld_global(p.rec + j * Base::RB);
-            d = static_cast<double>(dist2(r, s));
-            id = __float_as_int(r.w[1].w);
-        } else {
-            d = d_inf();
-            id = -1;
-        }
     }
 };
 
@@ -868,59 +851,64 @@ struct Fp64Vjp {
 // records so the inner loop has a fixed trip count.  Sinks whose own slot lies
 // in the current tile take the variant of the loop that skips the self pair.
 // ---------------------------------------------------------------------------
+// 16-byte words of shared-memory staging per source: predicted records, or
+// (fused prediction) the double-single cache of Sec. 2.2.4's j-particle data.
+template <class P, bool FUSED>
+__host__ __device__ constexpr int stage_words() {
+    if constexpr (FUSED && P::kCanFuse) return dscache_words(P::kOrder);
+    else return P::RB / 16;
+}
+
 template <class P, bool FUSED>
 __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *smem, int t, int64_t j0, int64_t j1) {
     const int tile = p.tile;
-    unsigned char *dst = smem + static_cast<size_t>(t % kStages) * tile * P::RB;
+    constexpr int W = stage_words<P, FUSED>();
+    unsigned char *dst = smem + static_cast<size_t>(t % kStages) * tile * W * 16;
     const int64_t tb = j0 + static_cast<int64_t>(t) * tile;
     const int64_t rem = j1 - tb;
     const int cnt = rem < tile ? static_cast<int>(rem) : tile;
-    constexpr int W = P::RB / 16;
-    if constexpr (FUSED && P::kCanFuse && is_paired<P>::value) {
-        // predict the tile's sources from the double-single cache (one per
-        // thread) straight into pair records: source c = lj + jl*m is half
-        // m & 1 of pair (m >> 1) * jl + lj
-        const int jl = p.jl;
-        for (int c = threadIdx.x; c < tile; c += blockDim.x) {
-            const int lj = c & (jl - 1), m = c / jl;
-            float *q = reinterpret_cast<float *>(dst + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
-            typename P::Rec r;
-            if (c < cnt) {
-                r = P::predict(p.dsc, tb + c, p.t_hi, p.t_lo);
-            } else {
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    const uint4 u = P::sentinel(w);
-                    r.w[w] = *reinterpret_cast<const float4 *>(&u);
-                }
-            }
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                q[8 * w] = r.w[w].x;
-                q[8 * w + 2] = r.w[w].y;
-                q[8 * w + 4] = r.w[w].z;
-                q[8 * w + 6] = r.w[w].w;
-            }
-        }
-    } else if constexpr (FUSED && P::kCanFuse) {
-        // predict the tile's sources from the double-single cache (one per thread)
-        for (int c = threadIdx.x; c < tile; c += blockDim.x) {
-            uint4 *d = reinterpret_cast<uint4 *>(dst + static_cast<size_t>(c) * P::RB);
-            if (c < cnt) {
-                const typename P::Rec r = P::predict(p.dsc, tb + c, p.t_hi, p.t_lo);
-#pragma unroll
-                for (int w = 0; w < W; ++w) d[w] = *reinterpret_cast<const uint4 *>(&r.w[w]);
-            } else {
-#pragma unroll
-                for (int w = 0; w < W; ++w) d[w] = P::sentinel(w);
-            }
-        }
+    if constexpr (FUSED && P::kCanFuse) {
+        // the tile's double-single cache words; predicted after they land
+        // (predict_tile), the ragged end becomes filler records there
+        const float4 *src = p.dsc + tb * W;
+        const int v16 = cnt * W;
+        for (int c = threadIdx.x; c < v16; c += blockDim.x) cp_async16(dst + 16 * c, src + c);
     } else {
         const unsigned char *src = p.rec + tb * P::RB;
         const int n16 = tile * W, v16 = cnt * W;
         for (int c = threadIdx.x; c < n16; c += blockDim.x) {
             if (c < v16) cp_async16(dst + 16 * c, src + 16 * static_cast<size_t>(c));
             else *reinterpret_cast<uint4 *>(dst + 16 * c) = P::sentinel(c % W);
+        }
+    }
+}
+
+// Predict a staged tile of double-single cache words (cnt real sources) to
+// t_hi + t_lo, written as pair records: source c = lj + jl*m is half m & 1 of
+// pair (m >> 1) * jl + lj.
+template <class P>
+__device__ __forceinline__ void predict_tile(const ForceParams &p, const unsigned char *st, unsigned char *q, int cnt,
+                                             int jl) {
+    constexpr int W = P::RB / 16;
+    for (int c = threadIdx.x; c < p.tile; c += blockDim.x) {
+        const int lj = c & (jl - 1), m = c / jl;
+        float *d = reinterpret_cast<float *>(q + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
+        typename P::Rec r;
+        if (c < cnt) {
+            r = P::predict(reinterpret_cast<const float4 *>(st), c, p.t_hi, p.t_lo);
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint4 u = P::sentinel(w);
+                r.w[w] = *reinterpret_cast<const float4 *>(&u);
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            d[8 * w] = r.w[w].x;
+            d[8 * w + 2] = r.w[w].y;
+            d[8 * w + 4] = r.w[w].z;
+            d[8 * w + 6] = r.w[w].w;
         }
     }
 }
@@ -966,7 +954,7 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
                     P::template interact2<SELF, false>(r, jb + u * jl, jl, u, sk[k], ac[k], eps2);
             }
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb);
+            for (int k = 0; k < IPT; ++k) P::fold(ac[k], jb, pq, pstep, sk[k]);
         }
     } else {
         for (int q0 = 0; q0 < per; q0 += P::kChunk) {
@@ -988,17 +976,120 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
     }
 }
 
+// Merge the j-lanes of a sink (paired policies): the double-single totals
+// are combined with double-single adds and the nearest-neighbour candidates
+// (FP32 distances) with FP32 compares, so the xor-butterfly never waits on
+// the FP64 pipe; the merged totals leave as FP64.
+template <class P>
+__device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, int jl, double *t, double &nd, int &nid) {
+    const float2 *t2 = reinterpret_cast<const float2 *>(tot);
+    ds q[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) q[f] = ds{t2[f * stride].x, t2[f * stride].y};
+    float d = static_cast<float>(nd);  // exact: an FP32 distance or +inf
+    for (int off = jl >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f)
+            q[f] = ds_add(q[f], ds{__shfl_xor_sync(kFull, q[f].h, off), __shfl_xor_sync(kFull, q[f].l, off)});
+        if (P::kNN) {
+            const float od = __shfl_xor_sync(kFull, d, off);
+            const int oid = __shfl_xor_sync(kFull, nid, off);
+            if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(nid))) {
+                d = od;
+                nid = oid;
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = static_cast<double>(q[f].h) + static_cast<double>(q[f].l);
+    t[P::NS - 1] = -t[P::NS - 1];
+    nd = static_cast<double>(d);
+}
+
+// FP64 reduction of one sink's slices (sink-major row: field f's slices are
+// contiguous) by the whole CTA, one warp per field: lane l of the warp sums
+// slices l, l+32, ... in order, a fixed xor-butterfly combines the lanes, and
+// the field totals meet in shared memory, where thread 0 writes the outputs
+// (write(t, d, id)).  Each warp works on a different field at the same time,
+// so the 1/64-rate FP64 adds of the fields run side by side on the SM's
+// sub-partitions.  The nearest-neighbour field (non-negative r^2, FP64) is
+// merged by comparing bit patterns as integers, which orders them like the
+// values.  Deterministic: the order of every sum is fixed.
+template <class P, class Write>
+__device__ __forceinline__ void reduce_sink_fields(const double *row, const int32_t *row_id, int split, double *s_f,
+                                                   long long &s_nd, int &s_nid, const Write &write) {
+    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int f = warp; f < NF; f += nw) {
+        const double *col = row + static_cast<int64_t>(f) * split;
+        if (f < P::NS) {
+            // slices lane, lane+32, ... added in order; loaded eight at a time
+            // so that the L2 round trips overlap
+            double v = 0.0;
+            int s = lane;
+            for (; s + 7 * 32 < split; s += 8 * 32) {
+                double x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = __ldcg(col + s + 32 * q);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v += x[q];
+            }
+            for (; s < split; s += 32) v += __ldcg(col + s);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+            if (lane == 0) s_f[f] = v;
+        } else {
+            long long d = 0x7ff0000000000000LL;  // +inf
+            int id = -1;
+            int s = lane;
+            for (; s + 7 * 32 < split; s += 8 * 32) {
+                long long xd[8];
+                int xi[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    xd[q] = __double_as_longlong(__ldcg(col + s + 32 * q));
+                    xi[q] = __ldcg(row_id + s + 32 * q);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (xd[q] < d || (xd[q] == d && static_cast<unsigned>(xi[q]) < static_cast<unsigned>(id))) { d = xd[q]; id = xi[q]; }
+            }
+            for (; s < split; s += 32) {
+                const long long od = __double_as_longlong(__ldcg(col + s));
+                const int oid = __ldcg(row_id + s);
+                if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const long long od = __shfl_xor_sync(kFull, d, off);
+                const int oid = __shfl_xor_sync(kFull, id, off);
+                if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
+            }
+            if (lane == 0) { s_nd = d; s_nid = id; }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t[P::NS];
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] = s_f[f];
+        write(t, P::kNN ? __longlong_as_double(s_nd) : d_inf(), P::kNN ? s_nid : -1);
+    }
+    __syncthreads();
+}
+
 // Fused split-j reduction of one i-block, run by the last CTA to finish one
 // of its slices.  Partials are read from L2 (__ldcg: written by other SMs in
 // this launch) in slice order, so the result does not depend on which CTA
 // arrives last.  Field-major partials (few slices): a thread per sink.
 // Sink-major partials (many slices): a warp per sink, or the whole CTA per
-// sink when the i-block has fewer sinks than the CTA has warps.
+// sink (a warp per field) when the i-block has fewer sinks than the CTA has
+// warps.
 template <class P>
 __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
-    __shared__ double s_t[kMaxThreads / 32][P::NS];
-    __shared__ double s_d[kMaxThreads / 32];
-    __shared__ int s_id[kMaxThreads / 32];
+    __shared__ double s_f[P::NS];
+    __shared__ long long s_nd;
+    __shared__ int s_nid;
     constexpr int NF = P::NS + (P::kNN ? 1 : 0);
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int64_t b0 = iblk * p.sinks_per_cta;
@@ -1022,10 +1113,15 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
         }
         return;
     }
-    const bool per_block = (b1 - b0) < nw;
-    const int lanes = per_block ? nt : 32;
-    const int me = per_block ? tid : lane;
-    for (int64_t i = per_block ? b0 : b0 + warp; i < b1; i += per_block ? 1 : nw) {
+    if (b1 - b0 < nw) {
+        // few sinks: the whole CTA on each, one warp per field
+        for (int64_t i = b0; i < b1; ++i)
+            reduce_sink_fields<P>(p.part + i * NF * split, p.part_id + i * split, split, s_f, s_nd, s_nid,
+                                  [&](const double *t, double d, int id) { P::write_final(p, i, t, d, id); });
+        return;
+    }
+    // a warp per sink
+    for (int64_t i = b0 + warp; i < b1; i += nw) {
         const double *row = p.part + i * NF * split;
         const int32_t *row_id = p.part_id + i * split;
         double t[P::NS];
@@ -1033,7 +1129,7 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
         for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
         double nd = d_inf();
         int nid = -1;
-        for (int s = me; s < split; s += lanes) {
+        for (int s = lane; s < split; s += 32) {
 #pragma unroll
             for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(row + f * split + s);
             if (P::kNN) nn_merge(nd, nid, __ldcg(row + P::NS * split + s), __ldcg(row_id + s));
@@ -1048,26 +1144,7 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
                 nn_merge(nd, nid, od, oid);
             }
         }
-        if (!per_block) {
-            if (lane == 0) P::write_final(p, i, t, nd, nid);
-            continue;
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int f = 0; f < P::NS; ++f) s_t[warp][f] = t[f];
-            s_d[warp] = nd;
-            s_id[warp] = nid;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < nw; ++w) {
-#pragma unroll
-                for (int f = 0; f < P::NS; ++f) t[f] += s_t[w][f];
-                if (P::kNN) nn_merge(nd, nid, s_d[w], s_id[w]);
-            }
-            P::write_final(p, i, t, nd, nid);
-        }
-        __syncthreads();
+        if (lane == 0) P::write_final(p, i, t, nd, nid);
     }
 }
 
@@ -1087,8 +1164,10 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
     const typename P::real eps2 = static_cast<typename P::real>(p.eps2);
     const int per = p.tile / jl;  // a multiple of P::kChunk (host-checked)
     constexpr bool kPair = is_paired<P>::value;
-    unsigned char *pbuf = smem + static_cast<size_t>(kStages) * p.tile * P::RB;  // pair records (kPair)
-    double *tot = reinterpret_cast<double *>(smem + static_cast<size_t>(kStages + (kPair ? 1 : 0)) * p.tile * P::RB) + tid;
+    static_assert(kPair || !FUSED, "fused prediction needs a paired policy");
+    const size_t ring_stride = static_cast<size_t>(p.tile) * stage_words<P, FUSED>() * 16;
+    unsigned char *pbuf = smem + kStages * ring_stride;  // pair records (kPair)
+    double *tot = reinterpret_cast<double *>(pbuf + (kPair ? static_cast<size_t>(p.tile) * P::RB : 0)) + tid;
 
     __shared__ int s_last;
     for (;;) {
@@ -1135,14 +1214,19 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             __syncthreads();
             if (t + kStages - 1 < n_tiles) load_tile<P, FUSED>(p, smem, t + kStages - 1, j0, j1);
             cp_async_commit();
-            const unsigned char *st = smem + static_cast<size_t>(t % kStages) * p.tile * P::RB;
-            if constexpr (kPair && !FUSED) {
+            const unsigned char *st = smem + (t % kStages) * ring_stride;
+            const int tb = static_cast<int>(j0) + t * p.tile;
+            if constexpr (kPair) {
                 // every thread has left the previous tile's pair records (barrier above)
-                pair_tile<P>(st, pbuf, p.tile, jl);
+                if constexpr (FUSED) {
+                    const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
+                    predict_tile<P>(p, st, pbuf, cnt, jl);
+                } else {
+                    pair_tile<P>(st, pbuf, p.tile, jl);
+                }
                 __syncthreads();
                 st = pbuf;
             }
-            const int tb = static_cast<int>(j0) + t * p.tile;
             const int te = (tb + p.tile < j1) ? tb + p.tile : static_cast<int>(j1);
             bool mine = false;
 #pragma unroll
@@ -1162,18 +1246,25 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
         for (int k = 0; k < IPT; ++k) {
             P::flush(ac[k], tot + k * P::NS * nt, nt);
             double t[P::NS];
-            P::totals(ac[k], tot + k * P::NS * nt, nt, t);
-            double nd;
-            int nid;
-            if constexpr (P::kCanFuse) P::template nn_lookup<FUSED>(ac[k], sk[k], p, p.j_end, jl, nd, nid);
-            else P::nn(ac[k], sk[k], p.rec, p.j_end, jl, nd, nid);
-            for (int off = jl >> 1; off > 0; off >>= 1) {
+            double nd = d_inf();
+            int nid = -1;
+            if constexpr (kPair) {
+                if (P::kNN && ac[k].bid >= 0) {
+                    nd = static_cast<double>(ac[k].bd);
+                    nid = ac[k].bid;
+                }
+                merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, t, nd, nid);
+            } else {
+                P::nn(ac[k], sk[k], p.rec, p.j_end, jl, nd, nid);
+                P::totals(ac[k], tot + k * P::NS * nt, nt, t);
+                for (int off = jl >> 1; off > 0; off >>= 1) {
 #pragma unroll
-                for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
-                if (P::kNN) {
-                    const double od = __shfl_xor_sync(kFull, nd, off);
-                    const int oid = __shfl_xor_sync(kFull, nid, off);
-                    nn_merge(nd, nid, od, oid);
+                    for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+                    if (P::kNN) {
+                        const double od = __shfl_xor_sync(kFull, nd, off);
+                        const int oid = __shfl_xor_sync(kFull, nid, off);
+                        nn_merge(nd, nid, od, oid);
+                    }
                 }
             }
             if (lj == 0 && val[k]) {
@@ -1272,59 +1363,16 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
 }
 
 // Few sinks, many slices: one 256-thread block per sink on the sink-major
-// layout.  Thread t sums slices t, t+256, ... in order; a fixed xor-butterfly
-// combines each warp and warp 0 adds the eight warp sums in order, so the
-// result does not depend on scheduling.  Many threads per sink keep many
-// loads in flight (a single warp walking 1000+ slices is latency bound).
+// layout, a warp per field (reduce_sink_fields).
 template <class P>
 __global__ void __launch_bounds__(256) reduce_block_kernel(const ReduceParams r) {
-    __shared__ double s_t[8][P::NS];
-    __shared__ double s_d[8];
-    __shared__ int s_id[8];
-    const int64_t i = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double s_f[P::NS];
+    __shared__ long long s_nd;
+    __shared__ int s_nid;
     constexpr int NF = P::NS + (P::kNN ? 1 : 0);
-    const double *row = r.part + i * NF * r.split;
-    const int32_t *row_id = r.part_id + i * r.split;
-    double t[P::NS];
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
-    double nd = d_inf();
-    int nid = -1;
-    for (int s = tid; s < r.split; s += 256) {
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
-        if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
-        if (P::kNN) {
-            const double od = __shfl_xor_sync(kFull, nd, off);
-            const int oid = __shfl_xor_sync(kFull, nid, off);
-            nn_merge(nd, nid, od, oid);
-        }
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) s_t[warp][f] = t[f];
-        s_d[warp] = nd;
-        s_id[warp] = nid;
-    }
-    __syncthreads();
-    if (tid == 0) {
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] = s_t[0][f];
-        nd = s_d[0];
-        nid = s_id[0];
-        for (int w = 1; w < 8; ++w) {
-#pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f] += s_t[w][f];
-            if (P::kNN) nn_merge(nd, nid, s_d[w], s_id[w]);
-        }
-        P::write_final(r, i, t, nd, nid);
-    }
+    const int64_t i = blockIdx.x;
+    reduce_sink_fields<P>(r.part + i * NF * r.split, r.part_id + i * r.split, r.split, s_f, s_nd, s_nid,
+                          [&](const double *t, double d, int id) { P::write_final(r, i, t, d, id); });
 }
 
 // ---------------------------------------------------------------------------
@@ -1442,9 +1490,10 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // ---------------------------------------------------------------------------
 // Dynamic shared memory of a pass launch: the record ring plus, for the mixed
 // policies, the FP64 totals of every (thread, sink, field).
-template <class P, int IPT>
+template <class P, int IPT, bool FUSED>
 inline size_t pass_smem(size_t ring_bytes, int threads) {
-    const size_t pair_bytes = is_paired<P>::value ? ring_bytes / kStages : 0;
+    const size_t tile = ring_bytes / (kStages * 16 * stage_words<P, FUSED>());
+    const size_t pair_bytes = is_paired<P>::value ? tile * P::RB : 0;
     return ring_bytes + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
 }
 
@@ -1453,7 +1502,7 @@ constexpr int kMaxDynSmem = 200 * 1024;
 template <class P, int IPT, bool FUSED>
 inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t ring_bytes, cudaStream_t s) {
     static bool attr_set = false;
-    const size_t smem = pass_smem<P, IPT>(ring_bytes, threads);
+    const size_t smem = pass_smem<P, IPT, FUSED>(ring_bytes, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) return cudaErrorInvalidConfiguration;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1467,7 +1516,7 @@ inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size
 
 template <class P, int IPT, bool FUSED>
 inline cudaError_t occupancy_pass(int threads, size_t ring_bytes, int *blocks) {
-    const size_t smem = pass_smem<P, IPT>(ring_bytes, threads);
+    const size_t smem = pass_smem<P, IPT, FUSED>(ring_bytes, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) {
         *blocks = 0;
         return cudaSuccess;

@@ -22,7 +22,7 @@ struct JStore {
     //   {axh ayh azh 0}{axl ayl azl 0}{jx jy jz 0}[{sx sy sz 0}]   (float4 words)
     float4 *dsc;
 };
-inline int dscache_words(int order) { return order == 6 ? 8 : 7; }
+__host__ __device__ constexpr int dscache_words(int order) { return order == 6 ? 8 : 7; }
 
 // Bytes of one predicted record.
 //   mixed H4: {xh yh zh m}{xl yl zl id}{vx vy vz 0}            48 B
