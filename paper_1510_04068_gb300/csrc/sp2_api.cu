@@ -62,7 +62,8 @@ struct sp2_ctx {
     unsigned char *rec2 = nullptr;  // records of the all-pairs / VJP entry points
     int32_t *iota = nullptr;
     double *tmp = nullptr;          // 4 x (n_max x 3) doubles: a1, j1, xpbar, vpbar
-    unsigned int *dev_words = nullptr;  // [0] work queue, [1] error flag, [2] finite flag
+    unsigned int *dev_words = nullptr;  // [0] batched work queue, [1] error flag, [2] finite flag,
+                                        // [4] pass work queue, [5] pass exit count (both self-resetting)
     double *part = nullptr;
     int32_t *part_id = nullptr;
     size_t part_cap = 0, part_id_cap = 0;   // bytes
@@ -302,6 +303,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     }
     const int64_t n_items = n_iblk * split;
     const int grid = static_cast<int>(std::min<int64_t>(n_items, static_cast<int64_t>(c->sm_count) * per_sm));
+    const int static_items = (grid == n_items) ? 1 : 0;  // one wave: CTA b takes item b
 
     ForceParams p{};
     p.rec = rec;
@@ -316,7 +318,9 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     p.sinks_per_cta = static_cast<int>(sinks_per_cta);
     p.n_iblk = n_iblk;
     p.n_items = n_items;
-    p.queue = c->dev_words;
+    p.queue = c->dev_words + 4;       // self-resetting work counter of the pass kernel
+    p.exit_count = c->dev_words + 5;
+    p.static_items = static_items;
     p.err = c->dev_words + 1;
     p.n_loaded = n_valid;
     p.eps2 = c->cfg.eps2;
@@ -346,7 +350,6 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
             p.done = c->done;
         }
     }
-    SP2_CK(c, cudaMemsetAsync(c->dev_words, 0, sizeof(unsigned int), c->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms_out) {
         cudaEventCreate(&e0);

@@ -890,25 +890,37 @@ template <class P>
 __device__ __forceinline__ void predict_tile(const ForceParams &p, const unsigned char *st, unsigned char *q, int cnt,
                                              int jl) {
     constexpr int W = P::RB / 16;
-    for (int c = threadIdx.x; c < p.tile; c += blockDim.x) {
-        const int lj = c & (jl - 1), m = c / jl;
-        float *d = reinterpret_cast<float *>(q + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
-        typename P::Rec r;
-        if (c < cnt) {
-            r = P::predict(reinterpret_cast<const float4 *>(st), c, p.t_hi, p.t_lo);
-        } else {
+    const int nt = blockDim.x;
+    const float4 *src = reinterpret_cast<const float4 *>(st);
+    // two sources per step, both predicted before either is stored (ILP)
+    for (int c0 = threadIdx.x; c0 < p.tile; c0 += 2 * nt) {
+        typename P::Rec r[2];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint4 u = P::sentinel(w);
-                r.w[w] = *reinterpret_cast<const float4 *>(&u);
+        for (int e = 0; e < 2; ++e) {
+            const int c = c0 + e * nt;
+            if (c < cnt) {
+                r[e] = P::predict(src, c, p.t_hi, p.t_lo);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const uint4 u = P::sentinel(w);
+                    r[e].w[w] = *reinterpret_cast<const float4 *>(&u);
+                }
             }
         }
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            d[8 * w] = r.w[w].x;
-            d[8 * w + 2] = r.w[w].y;
-            d[8 * w + 4] = r.w[w].z;
-            d[8 * w + 6] = r.w[w].w;
+        for (int e = 0; e < 2; ++e) {
+            const int c = c0 + e * nt;
+            if (c >= p.tile) break;
+            const int lj = c & (jl - 1), m = c / jl;
+            float *d = reinterpret_cast<float *>(q + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                d[8 * w] = r[e].w[w].x;
+                d[8 * w + 2] = r[e].w[w].y;
+                d[8 * w + 4] = r[e].w[w].z;
+                d[8 * w + 6] = r[e].w[w].w;
+            }
         }
     }
 }
@@ -1007,66 +1019,83 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
 }
 
 // FP64 reduction of one sink's slices (sink-major row: field f's slices are
-// contiguous) by the whole CTA, one warp per field: lane l of the warp sums
-// slices l, l+32, ... in order, a fixed xor-butterfly combines the lanes, and
-// the field totals meet in shared memory, where thread 0 writes the outputs
-// (write(t, d, id)).  Each warp works on a different field at the same time,
-// so the 1/64-rate FP64 adds of the fields run side by side on the SM's
-// sub-partitions.  The nearest-neighbour field (non-negative r^2, FP64) is
+// contiguous) by the whole CTA, fields spread over the warps: lane l of a
+// warp sums slices l, l+32, ... of a field in order, a fixed xor-butterfly
+// combines the lanes, and the field totals meet in shared memory, where
+// thread 0 writes the outputs (write(t, d, id)).  Different warps work on
+// different fields at the same time, so the 1/64-rate FP64 adds run side by
+// side on the SM's sub-partitions.  The nearest-neighbour field (non-negative r^2, FP64) is
 // merged by comparing bit patterns as integers, which orders them like the
 // values.  Deterministic: the order of every sum is fixed.
 template <class P, class Write>
 __device__ __forceinline__ void reduce_sink_fields(const double *row, const int32_t *row_id, int split, double *s_f,
                                                    long long &s_nd, int &s_nid, const Write &write) {
-    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int f = warp; f < NF; f += nw) {
-        const double *col = row + static_cast<int64_t>(f) * split;
-        if (f < P::NS) {
-            // slices lane, lane+32, ... added in order; loaded eight at a time
-            // so that the L2 round trips overlap
-            double v = 0.0;
-            int s = lane;
-            for (; s + 7 * 32 < split; s += 8 * 32) {
-                double x[8];
+    // sums: warp w takes fields w, w + nw, ... four at a time with their adds
+    // interleaved (independent FP64 chains keep the FP64 pipe busy)
+    for (int f0 = warp; f0 < P::NS; f0 += 4 * nw) {
+        bool on[4];
+        const double *col[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) x[q] = __ldcg(col + s + 32 * q);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v += x[q];
-            }
-            for (; s < split; s += 32) v += __ldcg(col + s);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-            if (lane == 0) s_f[f] = v;
-        } else {
-            long long d = 0x7ff0000000000000LL;  // +inf
-            int id = -1;
-            int s = lane;
-            for (; s + 7 * 32 < split; s += 8 * 32) {
-                long long xd[8];
-                int xi[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    xd[q] = __double_as_longlong(__ldcg(col + s + 32 * q));
-                    xi[q] = __ldcg(row_id + s + 32 * q);
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (xd[q] < d || (xd[q] == d && static_cast<unsigned>(xi[q]) < static_cast<unsigned>(id))) { d = xd[q]; id = xi[q]; }
-            }
-            for (; s < split; s += 32) {
-                const long long od = __double_as_longlong(__ldcg(col + s));
-                const int oid = __ldcg(row_id + s);
-                if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const long long od = __shfl_xor_sync(kFull, d, off);
-                const int oid = __shfl_xor_sync(kFull, id, off);
-                if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
-            }
-            if (lane == 0) { s_nd = d; s_nid = id; }
+        for (int q = 0; q < 4; ++q) {
+            on[q] = f0 + q * nw < P::NS;
+            col[q] = row + static_cast<int64_t>(on[q] ? f0 + q * nw : f0) * split;
         }
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        int s = lane;
+        for (; s + 3 * 32 < split; s += 4 * 32) {
+            double x[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[q][e] = on[q] ? __ldcg(col[q] + s + 32 * e) : 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[q] += x[q][e];
+        }
+        for (; s < split; s += 32)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (on[q]) v[q] += __ldcg(col[q] + s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (on[q]) s_f[f0 + q * nw] = v[q];
+    }
+    if (P::kNN && warp == nw - 1) {
+        const double *col = row + static_cast<int64_t>(P::NS) * split;
+        long long d = 0x7ff0000000000000LL;  // +inf
+        int id = -1;
+        int s = lane;
+        for (; s + 7 * 32 < split; s += 8 * 32) {
+            long long xd[8];
+            int xi[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                xd[q] = __double_as_longlong(__ldcg(col + s + 32 * q));
+                xi[q] = __ldcg(row_id + s + 32 * q);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (xd[q] < d || (xd[q] == d && static_cast<unsigned>(xi[q]) < static_cast<unsigned>(id))) { d = xd[q]; id = xi[q]; }
+        }
+        for (; s < split; s += 32) {
+            const long long od = __double_as_longlong(__ldcg(col + s));
+            const int oid = __ldcg(row_id + s);
+            if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const long long od = __shfl_xor_sync(kFull, d, off);
+            const int oid = __shfl_xor_sync(kFull, id, off);
+            if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
+        }
+        if (lane == 0) { s_nd = d; s_nid = id; }
     }
     __syncthreads();
     if (tid == 0) {
@@ -1170,14 +1199,32 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
     double *tot = reinterpret_cast<double *>(pbuf + (kPair ? static_cast<size_t>(p.tile) * P::RB : 0)) + tid;
 
     __shared__ int s_last;
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = atomicAdd(p.queue, 1u);
-        __syncthreads();
-        const int64_t item = s_item;
+    for (int round = 0;; ++round) {
+        int64_t item;
+        if (p.static_items) {
+            // one work item per CTA (grid == n_items): no counter to contend on
+            if (round > 0) break;
+            item = blockIdx.x;
+        } else {
+            __syncthreads();
+            if (tid == 0) s_item = atomicAdd(p.queue, 1u);
+            __syncthreads();
+            item = s_item;
+        }
         if (item >= p.n_items) break;
         const int64_t iblk = item % p.n_iblk;
         const int slice = static_cast<int>(item / p.n_iblk);
+
+        // the slice's first tiles are requested before the sinks are read, so
+        // the two memory round trips overlap
+        const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
+        const int64_t j1 = (j0 + p.slice_len < p.j_end) ? j0 + p.slice_len : p.j_end;
+        const int n_tiles = static_cast<int>((j1 - j0 + p.tile - 1) / p.tile);
+#pragma unroll
+        for (int s = 0; s < kStages - 1; ++s) {
+            if (s < n_tiles) load_tile<P, FUSED>(p, smem, s, j0, j1);
+            cp_async_commit();
+        }
 
         typename P::Sink sk[IPT];
         typename P::Acc ac[IPT];
@@ -1198,15 +1245,6 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             sk[k].slot = val[k] ? slot : -1;
             P::init(ac[k]);
             P::zero_totals(tot + k * P::NS * nt, nt);
-        }
-        const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
-        const int64_t j1 = (j0 + p.slice_len < p.j_end) ? j0 + p.slice_len : p.j_end;
-        const int n_tiles = static_cast<int>((j1 - j0 + p.tile - 1) / p.tile);
-
-#pragma unroll
-        for (int s = 0; s < kStages - 1; ++s) {
-            if (s < n_tiles) load_tile<P, FUSED>(p, smem, s, j0, j1);
-            cp_async_commit();
         }
         int since_flush = 0;
         for (int t = 0; t < n_tiles; ++t) {
@@ -1304,6 +1342,16 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
         }
     }
     cp_async_wait<0>();
+    if (p.exit_count && !p.static_items && tid == 0) {
+        // the last CTA out resets the work counter for the next launch (every
+        // CTA has taken its last item before it is counted here)
+        __threadfence();
+        if (atomicAdd(p.exit_count, 1u) == gridDim.x - 1) {
+            *p.queue = 0u;
+            *p.exit_count = 0u;
+            __threadfence();
+        }
+    }
 }
 
 // Second kernel of the source split: sum the slices of each sink in slice

@@ -52,6 +52,8 @@ struct ForceParams {
     int64_t n_iblk;            // i-blocks
     int64_t n_items;           // n_iblk * split
     unsigned int *queue;       // work-queue counter, zero at launch
+    unsigned int *exit_count;  // if set: CTAs count out and the last resets queue and exit_count to zero
+    int static_items;          // grid == n_items: CTA b takes item b and the queue is not used
     unsigned int *err;         // set to 1 when a sink slot is outside [0, n_loaded)
     int64_t n_loaded;
     double eps2;
