@@ -249,12 +249,12 @@ struct PassOut {
 };
 
 // Dynamic shared memory of a pass launch (the kernel side computes the same):
-// the kStages-deep staging ring (records, or double-single cache words when
-// the prediction is fused), for the mixed force passes one more tile of
+// the kStages-deep record ring (none when the prediction is fused: the pass
+// predicts each tile from global memory), for the mixed force passes one tile of
 // pair records, and for the mixed policies the FP64 totals of every
 // (thread, sink, field).
 size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
-    const size_t ring = static_cast<size_t>(kStagesDevice) * tile * (fused ? dscache_words(order) * 16 : rb);
+    const size_t ring = fused ? 0 : static_cast<size_t>(kStagesDevice) * tile * rb;
     const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
     const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
     return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);
@@ -288,9 +288,6 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
-    // the staging ring holds predicted records, or with fused prediction the
-    // double-single cache words of the sources
-    const size_t smem = static_cast<size_t>(kStagesDevice) * tile * (fused ? dscache_words(order) * 16 : rb);
     const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
     const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused);
     if (smem_total > 200 * 1024)
@@ -298,7 +295,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
     int per_sm = L.ctas_per_sm;
     if (per_sm <= 0) {
-        SP2_CK(c, force_kernel_occupancy(key, L.threads, smem, &per_sm));
+        SP2_CK(c, force_kernel_occupancy(key, L.threads, tile, &per_sm));
         if (per_sm <= 0) return fail(c, SP2_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
     }
     const int64_t n_items = n_iblk * split;
@@ -357,7 +354,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         cudaEventRecord(e0, c->stream);
     }
     ev_begin(c, stage_force);
-    SP2_CK(c, launch_force_kernel(key, p, grid, L.threads, smem, c->stream));
+    SP2_CK(c, launch_force_kernel(key, p, grid, L.threads, tile, c->stream));
     ev_end(c, stage_force);
     c->launches += 1;
     if (split > 1 && !p.fused_reduce) {
@@ -458,19 +455,19 @@ sp2_status finite_check(sp2_ctx *c, const double *const *arrs, const int64_t *le
 
 namespace sp2 {
 
-cudaError_t launch_force_kernel(const KernelKey &k, const ForceParams &p, int grid, int threads, size_t smem,
+cudaError_t launch_force_kernel(const KernelKey &k, const ForceParams &p, int grid, int threads, size_t tile,
                                 cudaStream_t s) {
-    if (k.kind == K_VJP) return k.mixed ? launch_force_vjpm(k, p, grid, threads, smem, s)
-                                        : launch_force_vjpd(k, p, grid, threads, smem, s);
-    if (k.order == 6) return k.mixed ? launch_force_h6m(k, p, grid, threads, smem, s)
-                                     : launch_force_h6d(k, p, grid, threads, smem, s);
-    return k.mixed ? launch_force_h4m(k, p, grid, threads, smem, s) : launch_force_h4d(k, p, grid, threads, smem, s);
+    if (k.kind == K_VJP) return k.mixed ? launch_force_vjpm(k, p, grid, threads, tile, s)
+                                        : launch_force_vjpd(k, p, grid, threads, tile, s);
+    if (k.order == 6) return k.mixed ? launch_force_h6m(k, p, grid, threads, tile, s)
+                                     : launch_force_h6d(k, p, grid, threads, tile, s);
+    return k.mixed ? launch_force_h4m(k, p, grid, threads, tile, s) : launch_force_h4d(k, p, grid, threads, tile, s);
 }
 
-cudaError_t force_kernel_occupancy(const KernelKey &k, int threads, size_t smem, int *b) {
-    if (k.kind == K_VJP) return k.mixed ? occupancy_force_vjpm(k, threads, smem, b) : occupancy_force_vjpd(k, threads, smem, b);
-    if (k.order == 6) return k.mixed ? occupancy_force_h6m(k, threads, smem, b) : occupancy_force_h6d(k, threads, smem, b);
-    return k.mixed ? occupancy_force_h4m(k, threads, smem, b) : occupancy_force_h4d(k, threads, smem, b);
+cudaError_t force_kernel_occupancy(const KernelKey &k, int threads, size_t tile, int *b) {
+    if (k.kind == K_VJP) return k.mixed ? occupancy_force_vjpm(k, threads, tile, b) : occupancy_force_vjpd(k, threads, tile, b);
+    if (k.order == 6) return k.mixed ? occupancy_force_h6m(k, threads, tile, b) : occupancy_force_h6d(k, threads, tile, b);
+    return k.mixed ? occupancy_force_h4m(k, threads, tile, b) : occupancy_force_h4d(k, threads, tile, b);
 }
 
 cudaError_t launch_reduce_kernel(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {
@@ -1040,10 +1037,9 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         int occ = 0;
         // the kernel run_pass will launch: fused prediction when the sinks fit one i-block
         const int fused = (mixed && c->js.dsc && n_i <= int64_t(L.threads / L.j_lanes) * L.i_per_thread) ? 1 : 0;
-        const size_t ring = static_cast<size_t>(kStagesDevice) * L.j_tile * (fused ? dscache_words(order) * 16 : c->rb);
         KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread, fused};
         if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, fused) > 200 * 1024 ||
-            force_kernel_occupancy(key, L.threads, ring, &occ) != cudaSuccess) {
+            force_kernel_occupancy(key, L.threads, L.j_tile, &occ) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }

@@ -851,55 +851,38 @@ struct Fp64Vjp {
 // records so the inner loop has a fixed trip count.  Sinks whose own slot lies
 // in the current tile take the variant of the loop that skips the self pair.
 // ---------------------------------------------------------------------------
-// 16-byte words of shared-memory staging per source: predicted records, or
-// (fused prediction) the double-single cache of Sec. 2.2.4's j-particle data.
-template <class P, bool FUSED>
-__host__ __device__ constexpr int stage_words() {
-    if constexpr (FUSED && P::kCanFuse) return dscache_words(P::kOrder);
-    else return P::RB / 16;
-}
-
-template <class P, bool FUSED>
+template <class P>
 __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *smem, int t, int64_t j0, int64_t j1) {
     const int tile = p.tile;
-    constexpr int W = stage_words<P, FUSED>();
-    unsigned char *dst = smem + static_cast<size_t>(t % kStages) * tile * W * 16;
+    constexpr int W = P::RB / 16;
+    unsigned char *dst = smem + static_cast<size_t>(t % kStages) * tile * P::RB;
     const int64_t tb = j0 + static_cast<int64_t>(t) * tile;
     const int64_t rem = j1 - tb;
     const int cnt = rem < tile ? static_cast<int>(rem) : tile;
-    if constexpr (FUSED && P::kCanFuse) {
-        // the tile's double-single cache words; predicted after they land
-        // (predict_tile), the ragged end becomes filler records there
-        const float4 *src = p.dsc + tb * W;
-        const int v16 = cnt * W;
-        for (int c = threadIdx.x; c < v16; c += blockDim.x) cp_async16(dst + 16 * c, src + c);
-    } else {
-        const unsigned char *src = p.rec + tb * P::RB;
-        const int n16 = tile * W, v16 = cnt * W;
-        for (int c = threadIdx.x; c < n16; c += blockDim.x) {
-            if (c < v16) cp_async16(dst + 16 * c, src + 16 * static_cast<size_t>(c));
-            else *reinterpret_cast<uint4 *>(dst + 16 * c) = P::sentinel(c % W);
-        }
+    const unsigned char *src = p.rec + tb * P::RB;
+    const int n16 = tile * W, v16 = cnt * W;
+    for (int c = threadIdx.x; c < n16; c += blockDim.x) {
+        if (c < v16) cp_async16(dst + 16 * c, src + 16 * static_cast<size_t>(c));
+        else *reinterpret_cast<uint4 *>(dst + 16 * c) = P::sentinel(c % W);
     }
 }
 
-// Predict a staged tile of double-single cache words (cnt real sources) to
-// t_hi + t_lo, written as pair records: source c = lj + jl*m is half m & 1 of
-// pair (m >> 1) * jl + lj.
+// Fused prediction of a tile: sources tb .. tb+cnt-1 predicted from the
+// double-single cache in global memory to t_hi + t_lo and written as pair
+// records (source c = lj + jl*m is half m & 1 of pair (m >> 1) * jl + lj);
+// the rest of the tile becomes filler records.  Two sources per thread and
+// step, both loaded and predicted before either is stored.
 template <class P>
-__device__ __forceinline__ void predict_tile(const ForceParams &p, const unsigned char *st, unsigned char *q, int cnt,
-                                             int jl) {
+__device__ __forceinline__ void predict_tile(const ForceParams &p, int64_t tb, int cnt, unsigned char *q, int jl) {
     constexpr int W = P::RB / 16;
     const int nt = blockDim.x;
-    const float4 *src = reinterpret_cast<const float4 *>(st);
-    // two sources per step, both predicted before either is stored (ILP)
     for (int c0 = threadIdx.x; c0 < p.tile; c0 += 2 * nt) {
         typename P::Rec r[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = c0 + e * nt;
             if (c < cnt) {
-                r[e] = P::predict(src, c, p.t_hi, p.t_lo);
+                r[e] = P::predict(p.dsc, tb + c, p.t_hi, p.t_lo);
             } else {
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -1194,7 +1177,9 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
     const int per = p.tile / jl;  // a multiple of P::kChunk (host-checked)
     constexpr bool kPair = is_paired<P>::value;
     static_assert(kPair || !FUSED, "fused prediction needs a paired policy");
-    const size_t ring_stride = static_cast<size_t>(p.tile) * stage_words<P, FUSED>() * 16;
+    // fused prediction writes pair records straight from global memory and
+    // needs no staging ring
+    const size_t ring_stride = FUSED ? 0 : static_cast<size_t>(p.tile) * P::RB;
     unsigned char *pbuf = smem + kStages * ring_stride;  // pair records (kPair)
     double *tot = reinterpret_cast<double *>(pbuf + (kPair ? static_cast<size_t>(p.tile) * P::RB : 0)) + tid;
 
@@ -1220,10 +1205,12 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
         const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
         const int64_t j1 = (j0 + p.slice_len < p.j_end) ? j0 + p.slice_len : p.j_end;
         const int n_tiles = static_cast<int>((j1 - j0 + p.tile - 1) / p.tile);
+        if constexpr (!FUSED) {
 #pragma unroll
-        for (int s = 0; s < kStages - 1; ++s) {
-            if (s < n_tiles) load_tile<P, FUSED>(p, smem, s, j0, j1);
-            cp_async_commit();
+            for (int s = 0; s < kStages - 1; ++s) {
+                if (s < n_tiles) load_tile<P>(p, smem, s, j0, j1);
+                cp_async_commit();
+            }
         }
 
         typename P::Sink sk[IPT];
@@ -1248,22 +1235,25 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
         }
         int since_flush = 0;
         for (int t = 0; t < n_tiles; ++t) {
-            cp_async_wait<kStages - 2>();
-            __syncthreads();
-            if (t + kStages - 1 < n_tiles) load_tile<P, FUSED>(p, smem, t + kStages - 1, j0, j1);
-            cp_async_commit();
-            const unsigned char *st = smem + (t % kStages) * ring_stride;
             const int tb = static_cast<int>(j0) + t * p.tile;
-            if constexpr (kPair) {
-                // every thread has left the previous tile's pair records (barrier above)
-                if constexpr (FUSED) {
-                    const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
-                    predict_tile<P>(p, st, pbuf, cnt, jl);
-                } else {
-                    pair_tile<P>(st, pbuf, p.tile, jl);
-                }
+            const unsigned char *st;
+            if constexpr (FUSED) {
+                __syncthreads();  // every thread has left the previous tile
+                predict_tile<P>(p, tb, (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb), pbuf, jl);
                 __syncthreads();
                 st = pbuf;
+            } else {
+                cp_async_wait<kStages - 2>();
+                __syncthreads();
+                if (t + kStages - 1 < n_tiles) load_tile<P>(p, smem, t + kStages - 1, j0, j1);
+                cp_async_commit();
+                st = smem + (t % kStages) * ring_stride;
+                if constexpr (kPair) {
+                    // every thread has left the previous tile's pair records (barrier above)
+                    pair_tile<P>(st, pbuf, p.tile, jl);
+                    __syncthreads();
+                    st = pbuf;
+                }
             }
             const int te = (tb + p.tile < j1) ? tb + p.tile : static_cast<int>(j1);
             bool mine = false;
@@ -1536,21 +1526,23 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // ---------------------------------------------------------------------------
 // Instantiation helpers for one (order, precision) translation unit.
 // ---------------------------------------------------------------------------
-// Dynamic shared memory of a pass launch: the record ring plus, for the mixed
-// policies, the FP64 totals of every (thread, sink, field).
+// Dynamic shared memory of a pass launch with tile records per stage: the
+// record ring (none with fused prediction), one tile of pair records (paired
+// policies) and, for the mixed policies, the totals of every (thread, sink,
+// field).  The launch and occupancy helpers take the tile, not bytes.
 template <class P, int IPT, bool FUSED>
-inline size_t pass_smem(size_t ring_bytes, int threads) {
-    const size_t tile = ring_bytes / (kStages * 16 * stage_words<P, FUSED>());
+inline size_t pass_smem(size_t tile, int threads) {
+    const size_t ring = FUSED ? 0 : kStages * tile * P::RB;
     const size_t pair_bytes = is_paired<P>::value ? tile * P::RB : 0;
-    return ring_bytes + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
+    return ring + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
 }
 
 constexpr int kMaxDynSmem = 200 * 1024;
 
 template <class P, int IPT, bool FUSED>
-inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t ring_bytes, cudaStream_t s) {
+inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t tile, cudaStream_t s) {
     static bool attr_set = false;
-    const size_t smem = pass_smem<P, IPT, FUSED>(ring_bytes, threads);
+    const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) return cudaErrorInvalidConfiguration;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1563,8 +1555,8 @@ inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size
 }
 
 template <class P, int IPT, bool FUSED>
-inline cudaError_t occupancy_pass(int threads, size_t ring_bytes, int *blocks) {
-    const size_t smem = pass_smem<P, IPT, FUSED>(ring_bytes, threads);
+inline cudaError_t occupancy_pass(int threads, size_t tile, int *blocks) {
+    const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) {
         *blocks = 0;
         return cudaSuccess;
@@ -1576,26 +1568,26 @@ inline cudaError_t occupancy_pass(int threads, size_t ring_bytes, int *blocks) {
 }
 
 template <class P, bool FUSED>
-inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t smem,
+inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
                                   cudaStream_t s, int *blocks) {
     switch (ipt) {
-        case 1: return occ ? occupancy_pass<P, 1, FUSED>(threads, smem, blocks) : launch_pass<P, 1, FUSED>(*p, grid, threads, smem, s);
-        case 2: return occ ? occupancy_pass<P, 2, FUSED>(threads, smem, blocks) : launch_pass<P, 2, FUSED>(*p, grid, threads, smem, s);
-        case 4: return occ ? occupancy_pass<P, 4, FUSED>(threads, smem, blocks) : launch_pass<P, 4, FUSED>(*p, grid, threads, smem, s);
+        case 1: return occ ? occupancy_pass<P, 1, FUSED>(threads, tile, blocks) : launch_pass<P, 1, FUSED>(*p, grid, threads, tile, s);
+        case 2: return occ ? occupancy_pass<P, 2, FUSED>(threads, tile, blocks) : launch_pass<P, 2, FUSED>(*p, grid, threads, tile, s);
+        case 4: return occ ? occupancy_pass<P, 4, FUSED>(threads, tile, blocks) : launch_pass<P, 4, FUSED>(*p, grid, threads, tile, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 // fused = 1 is available for the mixed force policies only
 template <class P>
-inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t smem,
+inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
                                 cudaStream_t s, int *blocks, int fused = 0) {
-    if constexpr (P::kCanFuse) {
-        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, smem, s, blocks);
+    if constexpr (P::kCanFuse && is_paired<P>::value) {
+        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, tile, s, blocks);
     } else {
         if (fused) return cudaErrorInvalidValue;
     }
-    return dispatch_ipt_f<P, false>(occ, ipt, p, grid, threads, smem, s, blocks);
+    return dispatch_ipt_f<P, false>(occ, ipt, p, grid, threads, tile, s, blocks);
 }
 
 template <class P>
@@ -1636,16 +1628,16 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
 #define SP2_DEFINE_FORCE_TU(SUFFIX, POLICY, BATCH_POLICY, ORDER)                                           \
     namespace sp2 {                                                                                        \
     cudaError_t launch_force_##SUFFIX(const KernelKey &k, const ForceParams &p, int grid, int threads,     \
-                                      size_t smem, cudaStream_t s) {                                       \
-        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, smem, s, nullptr,  \
+                                      size_t tile, cudaStream_t s) {                                       \
+        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, tile, s, nullptr,  \
                                                         k.fused)                                           \
-                    : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, smem, s, nullptr, \
+                    : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, tile, s, nullptr, \
                                                          k.fused);                                         \
     }                                                                                                      \
-    cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t smem, int *blocks) {       \
-        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks,  \
+    cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t tile, int *blocks) {       \
+        return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks,  \
                                                         k.fused)                                           \
-                    : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks, \
+                    : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks, \
                                                          k.fused);                                         \
     }                                                                                                      \
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {        \

@@ -127,10 +127,11 @@ struct KernelKey {
 };
 
 // Each kernel translation unit provides these for its (order, precision).
-// They return cudaErrorInvalidValue for a key they do not hold.
+// They return cudaErrorInvalidValue for a key they do not hold.  tile: the
+// sources per shared-memory stage (the kernels size their shared memory).
 cudaError_t launch_force_kernel(const KernelKey &k, const ForceParams &p, int grid, int threads,
-                                size_t smem, cudaStream_t s);
-cudaError_t force_kernel_occupancy(const KernelKey &k, int threads, size_t smem, int *blocks_per_sm);
+                                size_t tile, cudaStream_t s);
+cudaError_t force_kernel_occupancy(const KernelKey &k, int threads, size_t tile, int *blocks_per_sm);
 cudaError_t launch_reduce_kernel(const KernelKey &k, const ReduceParams &p, cudaStream_t s);
 cudaError_t launch_batched_kernel(int order, int mixed, int nn, const BatchParams &p, int grid,
                                   int threads, cudaStream_t s);

@@ -7,11 +7,11 @@ namespace sp2 {
 
 #define SP2_VJP_TU(SUFFIX, POLICY)                                                                      \
     cudaError_t launch_force_##SUFFIX(const KernelKey &k, const ForceParams &p, int grid, int threads,  \
-                                      size_t smem, cudaStream_t s) {                                    \
-        return dispatch_ipt<POLICY>(false, k.ipt, &p, grid, threads, smem, s, nullptr, k.fused);        \
+                                      size_t tile, cudaStream_t s) {                                    \
+        return dispatch_ipt<POLICY>(false, k.ipt, &p, grid, threads, tile, s, nullptr, k.fused);        \
     }                                                                                                   \
-    cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t smem, int *blocks) {    \
-        return dispatch_ipt<POLICY>(true, k.ipt, nullptr, 0, threads, smem, 0, blocks, k.fused);        \
+    cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t tile, int *blocks) {    \
+        return dispatch_ipt<POLICY>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks, k.fused);        \
     }                                                                                                   \
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &, const ReduceParams &r, cudaStream_t s) {      \
         return launch_reduce<POLICY>(r, s);                                                             \

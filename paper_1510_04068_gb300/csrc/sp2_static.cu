@@ -30,7 +30,6 @@ constexpr int64_t kStaticMaxSources = 65536;
 constexpr int kMaxDevices = 64;
 constexpr int kRecBytes = 48;   // mixed Hermite-4 predicted record
 constexpr int kFields = 7;      // acc, jerk, pot
-constexpr int kStages = 3;      // pipeline depth of the pass kernel
 
 }  // namespace
 
@@ -126,9 +125,8 @@ extern "C" sp2_status sp2_step_static(int64_t n_j, const int32_t *id, const doub
     if (launch_predict(4, 1, js, n_j, t, rec, s) != cudaSuccess) return SP2_ERR_CUDA;
 
     KernelKey key{K_FORCE, 4, 1, nn, L.i_per_thread};
-    const size_t smem = static_cast<size_t>(kStages) * L.j_tile * kRecBytes;
     int per_sm = 0;
-    if (force_kernel_occupancy(key, L.threads, smem, &per_sm) != cudaSuccess || per_sm <= 0) return SP2_ERR_CUDA;
+    if (force_kernel_occupancy(key, L.threads, L.j_tile, &per_sm) != cudaSuccess || per_sm <= 0) return SP2_ERR_CUDA;
     ForceParams fp{};
     fp.rec = rec;
     fp.i_idx = i_idx;
@@ -157,7 +155,7 @@ extern "C" sp2_status sp2_step_static(int64_t n_j, const int32_t *id, const doub
     fp.part_id = part_id;
     fp.sink_major = split >= kWarpReduceMinSplit ? 1 : 0;
     const int grid = static_cast<int>(std::min<int64_t>(fp.n_items, static_cast<int64_t>(sms) * per_sm));
-    if (launch_force_kernel(key, fp, grid, L.threads, smem, s) != cudaSuccess) return SP2_ERR_CUDA;
+    if (launch_force_kernel(key, fp, grid, L.threads, L.j_tile, s) != cudaSuccess) return SP2_ERR_CUDA;
     if (split > 1) {
         ReduceParams r{};
         r.part = part;
