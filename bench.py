@@ -55,8 +55,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=131072)
     p.add_argument("--n-active", type=int, default=131072)
-    p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint lines")
-    p.add_argument("--extras", default="sweep,h6,batched,adjoint",
+    p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint / lists lines")
+    p.add_argument("--extras", default="sweep,h6,batched,adjoint,nb",
                    help="comma-separated secondary sections to run: sweep, h6, batched, adjoint")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -420,6 +420,8 @@ def extras(sp2, w, n, eps2, dev, stream, sections):
             res["batched"] = bench_batched(sp2, dev, stream)
         if "adjoint" in sections:
             res["adjoint"] = bench_adjoint(dev, stream)
+        if "nb" in sections:
+            res["nb"] = bench_nb(sp2, dev, stream)
     return res
 
 
@@ -515,6 +517,43 @@ def bench_h6(sp2, dev, stream):
         rows.append(row)
     for c in ctxs.values():
         c.close()
+    return rows
+
+
+def bench_nb(sp2, dev, stream):
+    """Neighbour lists (radius search riding on the force pass): Plummer
+    N = 131072, mixed Hermite-4 + NN, N_active = 16384 and 131072, h^2 = 2.5e-3
+    for every sink, capacity 256; the same step with and without lists."""
+    import torch
+    n = 131072
+    m, x, v = W.plummer(n, 0)
+    a, jk, _ = W.derivative_noise(n, 1, scales=(1.0, 4.0, 16.0))
+    ids = W.particle_ids(n)
+    tj = W.block_times(n, 2, 1.0)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    c = sp2.Context(order=4, precision=sp2.SP2_MIXED, n_max=n, eps2=1e-8, cuda_stream=stream.cuda_stream)
+    c.set_j(0, D(ids), D(m), D(x), D(v), D(a), D(jk), None, D(tj))
+    c.predict(1.0)
+    rows = []
+    for na in (16384, 131072):
+        idx = D(W.active_set(n, na, 3000 + na)) if na < n else D(np.arange(n, dtype=np.int32))
+        o = dict(acc=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 jerk=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                 pot=torch.empty(na, dtype=torch.float64, device=dev),
+                 nn_id=torch.empty(na, dtype=torch.int32, device=dev),
+                 nn_r2=torch.empty(na, dtype=torch.float64, device=dev))
+        h2 = torch.full((na,), 2.5e-3, dtype=torch.float64, device=dev)
+        cnt = torch.empty(na, dtype=torch.int32, device=dev)
+        lst = torch.empty((na, 256), dtype=torch.int32, device=dev)
+        c.autotune(na)
+        ms0 = timed(lambda: (c.predict(1.0), c.compute(idx, **o)), 3, stream)
+        ms1 = timed(lambda: (c.predict(1.0), c.compute_nb(idx, h2, 256, cnt, lst, **o)), 3, stream)
+        cc = cnt.cpu().numpy()
+        rows.append({"n_active": na, "us_per_step_no_lists": 1e3 * ms0, "us_per_step_with_lists": 1e3 * ms1,
+                     "interactions_per_s_with_lists": na * n / (ms1 / 1e3), "list_overhead": ms1 / ms0,
+                     "mean_neighbours": float(cc.mean()), "max_neighbours": int(cc.max()),
+                     "overflowed": int((cc > 256).sum())})
+    c.close()
     return rows
 
 

@@ -155,6 +155,31 @@ sp2_status sp2_compute_range(sp2_ctx *ctx, int64_t j_begin, int64_t j_end,
                              double *acc, double *jerk, double *snap, double *pot,
                              int32_t *nn_id, double *nn_r2, int ptr_kind);
 
+/* sp2_compute plus neighbour lists (Sec. 1: the library can return, for each
+ * particle, the list of all particles within a given radius; Sec. 3: the
+ * perturber lists of NBODY4-style integrators).  For sink k (position k of
+ * i_idx) the neighbours are the other loaded particles j with unsoftened
+ * |x_j - x_k|^2 < h2[k] (strict; the particle itself is never listed), r^2
+ * formed as in the force pass (exact FP64, or the FP32 double-single
+ * difference in mixed precision).
+ *   h2       [n_i] double, squared radius per sink (<= 0: no neighbours).
+ *   nb_max   list capacity per sink, 1 .. 4096.
+ *   nb_count [n_i] int32 out: number of neighbours found.  A value above
+ *            nb_max means the list overflowed: nb_max of the neighbours are
+ *            listed (which ones is not defined) and the caller may retry with
+ *            a smaller radius or a larger capacity.
+ *   nb_ids   [n_i x nb_max] int32 out: row k holds min(nb_count[k], nb_max)
+ *            neighbour ids in ascending order; the rest of the row is
+ *            unspecified.
+ * Needs a context opened with with_nn = 1 (the lists ride on the nearest-
+ * neighbour kernels; nn_id / nn_r2 may still be NULL).  Runs with one sink per
+ * thread.  Other arguments, layouts and errors as sp2_compute. */
+sp2_status sp2_compute_nb(sp2_ctx *ctx, int64_t n_i, const int32_t *i_idx,
+                          double *acc, double *jerk, double *snap, double *pot,
+                          int32_t *nn_id, double *nn_r2,
+                          const double *h2, int32_t nb_max, int32_t *nb_count,
+                          int32_t *nb_ids, int ptr_kind);
+
 /* Many independent systems (the few-body / planetary regime of Sec. 2.1):
  * system s owns the loaded slots offsets[s] .. offsets[s+1]-1 (host int64
  * array of n_sys + 1 increasing entries, offsets[n_sys] <= loaded), every

@@ -10,6 +10,8 @@ Contents
 ``predict``           Taylor predictor of the sources (Sec. 2.2), sp2_oracle.c
 ``forces``            direct sum of acc / jerk / snap / pot / nearest neighbour
                       with per-sink scale sums (Sec. 3), sp2_oracle.c
+``neighbours``        lists of the particles within a radius of each sink
+                      (Sec. 1, Sec. 3), sp2_oracle.c
 ``step``              predict + forces on sink slots, the block-step pass
 ``energy``            kinetic + potential energy
 ``hermite4_shared``   shared-step 4th-order Hermite integrator (test driver)
@@ -18,7 +20,8 @@ Contents
 Parity status: every output is pinned by the ``-m "not gpu"`` tests
 (brute force in 50-digit decimal arithmetic, two-body Kepler closed form,
 Newton's third law, pair-sum symmetry, finite differences along the predictor,
-invariances, Hermite energy conservation).
+invariances, Hermite energy conservation; neighbour lists against scipy's
+pairwise distances on an exact integer grid, symmetry, strictness, overflow).
 """
 from __future__ import annotations
 
@@ -61,6 +64,8 @@ def _load():
                                     ctypes.c_double, ctypes.c_int,
                                     P, P, P, P, P, P, P, P, P]
         lib.sp2o_forces.restype = None
+        lib.sp2o_neighbours.argtypes = [I64, P, P, P, I64, P, P, ctypes.c_int32, P, P]
+        lib.sp2o_neighbours.restype = None
         lib.sp2o_max_threads.restype = ctypes.c_int
         lib.sp2o_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -141,6 +146,23 @@ def forces(ids_i, xi, vi, ids_j, mj, xj, vj, eps2: float, order: int = 4, ai=Non
     if order != 6:
         del out["snap"], out["sc_snap"]
     return out
+
+
+def neighbours(ids_i, xi, h2, ids_j, xj, nb_max: int):
+    """Neighbour lists (sp2o_neighbours): count[n_i] and ids[n_i, nb_max], each
+    row's first min(count, nb_max) entries ascending (the smallest ids on
+    overflow); the rest of a row is -1."""
+    lib = _load()
+    ids_i = np.ascontiguousarray(ids_i, dtype=np.int32)
+    ids_j = np.ascontiguousarray(ids_j, dtype=np.int32)
+    xi = _f64(xi, (len(ids_i), 3))
+    xj = _f64(xj, (len(ids_j), 3))
+    h2 = _f64(h2, (len(ids_i),))
+    count = np.zeros(len(ids_i), dtype=np.int32)
+    out = np.full((len(ids_i), nb_max), -1, dtype=np.int32)
+    lib.sp2o_neighbours(ctypes.c_int64(len(ids_i)), _p(ids_i), _p(xi), _p(h2), ctypes.c_int64(len(ids_j)), _p(ids_j),
+                        _p(xj), ctypes.c_int32(nb_max), _p(count), _p(out))
+    return count, out
 
 
 def step(t, i_idx, ids, m, tj, x, v, a, jerk, snap=None, *, eps2: float, order: int = 4,

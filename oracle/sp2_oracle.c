@@ -185,3 +185,42 @@ void sp2o_forces(int64_t n_i, const int32_t *id_i, const double *xi, const doubl
         if (sc_snap) sc_snap[i] = Sh;
     }
 }
+
+/*
+ * Neighbour lists.  The paper (Sec. 1) states that the library can return, for
+ * each particle, the list of all particles within a given radius, and Sec. 3
+ * uses them as the perturber lists of NBODY4-style integrators.  For sink i
+ * (position i of the sink arrays) the neighbours are the sources j whose id
+ * differs from the sink's and whose unsoftened r.r is below h2[i] (strictly),
+ * r.r formed exactly as in sp2o_forces (left to right, no FMA).
+ *   count[i]                 number of neighbours;
+ *   ids[i * nb_max + k]      k < min(count[i], nb_max): the neighbour ids in
+ *                            ascending order (the nb_max smallest when the
+ *                            list overflows).
+ */
+void sp2o_neighbours(int64_t n_i, const int32_t *id_i, const double *xi, const double *h2,
+                     int64_t n_j, const int32_t *id_j, const double *xj,
+                     int32_t nb_max, int32_t *count, int32_t *ids)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n_i; ++i) {
+        int32_t c = 0;
+        int32_t *row = ids + i * (int64_t)nb_max;
+        for (int64_t j = 0; j < n_j; ++j) {
+            if (id_j[j] == id_i[i]) continue;
+            double r[3];
+            for (int k = 0; k < 3; ++k) r[k] = xj[3 * j + k] - xi[3 * i + k];
+            const double d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            if (!(d2 < h2[i])) continue;
+            /* insert id_j[j] into the sorted row, keeping the nb_max smallest */
+            const int32_t v = id_j[j];
+            int32_t n = c < nb_max ? c : nb_max;
+            if (n == nb_max && v >= row[n - 1]) { ++c; continue; }
+            int32_t q = (n == nb_max) ? n - 1 : n;
+            while (q > 0 && row[q - 1] > v) { row[q] = row[q - 1]; --q; }
+            row[q] = v;
+            ++c;
+        }
+        count[i] = c;
+    }
+}

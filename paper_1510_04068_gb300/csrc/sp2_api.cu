@@ -246,6 +246,10 @@ struct PassOut {
     double *nn_r2 = nullptr;
     double *xbar = nullptr, *vbar = nullptr, *mbar = nullptr;
     int accumulate = 0;
+    // neighbour lists (optional): squared radii per sink, capacity, counts, lists
+    const double *nb_h2 = nullptr;
+    int nb_max = 0;
+    int32_t *nb_count = nullptr, *nb_list = nullptr;
 };
 
 // Dynamic shared memory of a pass launch (the kernel side computes the same):
@@ -277,6 +281,8 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         auto it = (kind == K_FORCE) ? c->tuned.find(bucket_of(n_i)) : c->tuned.end();
         L = (it != c->tuned.end()) ? it->second : heuristic(c, kind, mixed, n_i, j_end - j_begin);
     }
+    const int nb = (kind == K_FORCE && nn && o.nb_count) ? 1 : 0;
+    if (nb) L.i_per_thread = 1;  // neighbour-list kernels take one sink per thread
     const int64_t n_j = j_end - j_begin;
     const int jl = L.j_lanes;
     int tile = L.j_tile;
@@ -284,7 +290,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     const int64_t n_iblk = ceil_div(n_i, sinks_per_cta);
     const int fused = (allow_fused && kind == K_FORCE && mixed && c->js.dsc && n_iblk == 1) ? 1 : 0;
     if (!fused && allow_fused) SP2_CKS(materialize(c));
-    KernelKey key{kind, order, mixed, nn, L.i_per_thread, fused};
+    KernelKey key{kind, order, mixed, nn, L.i_per_thread, fused, nb};
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
@@ -323,6 +329,13 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     p.eps2 = c->cfg.eps2;
     p.acc = o.acc; p.jerk = o.jerk; p.snap = o.snap; p.pot = o.pot; p.nn_id = o.nn_id; p.nn_r2 = o.nn_r2;
     p.xbar = o.xbar; p.vbar = o.vbar; p.mbar = o.mbar; p.accumulate = o.accumulate;
+    if (nb) {
+        p.nb_h2 = o.nb_h2;
+        p.nb_count = o.nb_count;
+        p.nb_list = o.nb_list;
+        p.nb_max = o.nb_max;
+        SP2_CK(c, cudaMemsetAsync(o.nb_count, 0, static_cast<size_t>(n_i) * sizeof(int32_t), c->stream));
+    }
     if (fused) {
         p.dsc = c->js.dsc;
         p.t_hi = static_cast<float>(c->t_pred);
@@ -368,6 +381,11 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         ev_begin(c, ST_REDUCE);
         SP2_CK(c, launch_reduce_kernel(key, r, c->stream));
         ev_end(c, ST_REDUCE);
+        c->launches += 1;
+    }
+    if (nb) {
+        // slots -> ids, each list sorted by id
+        SP2_CK(c, launch_nb_finish(c->js.id, n_i, o.nb_max, o.nb_count, o.nb_list, c->stream));
         c->launches += 1;
     }
     if (ms_out) {
@@ -710,9 +728,11 @@ sp2_status sp2_predict(sp2_ctx *c, double t) {
     return SP2_OK;
 }
 
-sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t n_i, const int32_t *i_idx,
-                             double *acc, double *jerk, double *snap, double *pot, int32_t *nn_id, double *nn_r2,
-                             int ptr_kind) {
+// sp2_compute_range / sp2_compute_nb: the force pass over sources [j_begin, j_end),
+// with neighbour lists when h2 is given.
+static sp2_status compute_impl(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t n_i, const int32_t *i_idx,
+                               double *acc, double *jerk, double *snap, double *pot, int32_t *nn_id, double *nn_r2,
+                               const double *h2, int32_t nb_max, int32_t *nb_count, int32_t *nb_ids, int ptr_kind) {
     SP2_CKS(usable(c));
     SP2_CKS(check_ptr_kind(c, ptr_kind));
     if (n_i < 0) return fail(c, SP2_ERR_ARG, "n_i < 0");
@@ -725,6 +745,13 @@ sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t
     if (n_i > (int64_t(1) << 30)) return fail(c, SP2_ERR_RANGE, "n_i too large");
     if (snap && c->cfg.order != 6) return fail(c, SP2_ERR_ARG, "snap requested from an order-4 context");
     if ((nn_id || nn_r2) && !c->cfg.with_nn) return fail(c, SP2_ERR_UNSUPPORTED, "context opened without nearest neighbour");
+    const bool want_nb = h2 || nb_count || nb_ids;
+    if (want_nb) {
+        if (!h2 || !nb_count || !nb_ids) return fail(c, SP2_ERR_ARG, "neighbour lists need h2, nb_count and nb_ids");
+        if (nb_max <= 0 || nb_max > 4096) return fail(c, SP2_ERR_ARG, "nb_max must be in [1, 4096]");
+        if (!c->cfg.with_nn) return fail(c, SP2_ERR_UNSUPPORTED, "neighbour lists need a context with nearest neighbour");
+        if (static_cast<double>(n_i) * nb_max > 2e9) return fail(c, SP2_ERR_RANGE, "n_i * nb_max too large");
+    }
     const int mixed = c->cfg.precision == SP2_MIXED;
     PassOut o;
     Staging s{c};
@@ -735,6 +762,7 @@ sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t
                 return fail(c, SP2_ERR_RANGE, "sink slot %d outside the loaded set", i_idx[k]);
         const size_t v3 = 3 * n_i * sizeof(double), v1 = n_i * sizeof(double);
         s.plan(n_i * 4); s.plan(v3); s.plan(v3); s.plan(v3); s.plan(v1); s.plan(n_i * 4); s.plan(v1);
+        if (want_nb) { s.plan(v1); s.plan(n_i * 4); s.plan(static_cast<size_t>(n_i) * nb_max * 4); }
         SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->stage), &c->stage_cap, s.total, "staging"));
         d_idx = stage_in(s, i_idx, n_i);
         o.acc = stage_out(s, acc, 3 * n_i);
@@ -743,11 +771,19 @@ sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t
         o.pot = stage_out(s, pot, n_i);
         o.nn_id = stage_out(s, nn_id, n_i);
         o.nn_r2 = stage_out(s, nn_r2, n_i);
+        if (want_nb) {
+            o.nb_h2 = stage_in(s, h2, n_i);
+            o.nb_count = stage_out(s, nb_count, n_i);
+            o.nb_list = stage_out(s, nb_ids, static_cast<size_t>(n_i) * nb_max);
+        }
         SP2_CKS(stage_copy_in(s));
     } else {
         o.acc = acc; o.jerk = jerk; o.snap = snap; o.pot = pot; o.nn_id = nn_id; o.nn_r2 = nn_r2;
+        o.nb_h2 = h2; o.nb_count = nb_count; o.nb_list = nb_ids;
     }
-    const int nn = c->cfg.with_nn && (o.nn_id || o.nn_r2);
+    o.nb_max = nb_max;
+    // the neighbour-list kernels are the nearest-neighbour kernels with lists
+    const int nn = c->cfg.with_nn && (o.nn_id || o.nn_r2 || want_nb);
     SP2_CKS(run_pass(c, K_FORCE, c->cfg.order, mixed, nn, c->rec, c->rb, c->n_loaded, d_idx, n_i, j_begin, j_end, o,
                      nullptr, ST_FORCE, nullptr, true));
     const double *arrs[4] = {o.acc, o.jerk, o.snap, o.pot};
@@ -757,11 +793,28 @@ sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t
     return SP2_OK;
 }
 
+sp2_status sp2_compute_range(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64_t n_i, const int32_t *i_idx,
+                             double *acc, double *jerk, double *snap, double *pot, int32_t *nn_id, double *nn_r2,
+                             int ptr_kind) {
+    return compute_impl(c, j_begin, j_end, n_i, i_idx, acc, jerk, snap, pot, nn_id, nn_r2, nullptr, 0, nullptr,
+                        nullptr, ptr_kind);
+}
+
 sp2_status sp2_compute(sp2_ctx *c, int64_t n_i, const int32_t *i_idx, double *acc, double *jerk, double *snap,
                        double *pot, int32_t *nn_id, double *nn_r2, int ptr_kind) {
     SP2_CKS(usable(c));
     if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
     return sp2_compute_range(c, 0, c->n_loaded, n_i, i_idx, acc, jerk, snap, pot, nn_id, nn_r2, ptr_kind);
+}
+
+sp2_status sp2_compute_nb(sp2_ctx *c, int64_t n_i, const int32_t *i_idx, double *acc, double *jerk, double *snap,
+                          double *pot, int32_t *nn_id, double *nn_r2, const double *h2, int32_t nb_max,
+                          int32_t *nb_count, int32_t *nb_ids, int ptr_kind) {
+    SP2_CKS(usable(c));
+    if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
+    if (!h2 || !nb_count || !nb_ids) return fail(c, SP2_ERR_ARG, "neighbour lists need h2, nb_count and nb_ids");
+    return compute_impl(c, 0, c->n_loaded, n_i, i_idx, acc, jerk, snap, pot, nn_id, nn_r2, h2, nb_max, nb_count,
+                        nb_ids, ptr_kind);
 }
 
 sp2_status sp2_batch_plan_create(sp2_ctx *c, int64_t n_sys, const int64_t *offsets, sp2_batch_plan **plan) {

@@ -383,9 +383,10 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
         return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     }
     // Sources a (slot j, chunk position u) and b (slot j + jl, position u + 1).
+    // Returns the pair's unsoftened r^2 (used by the neighbour-list policy).
     template <bool SELF, bool FIRST>
-    __device__ static __forceinline__ void interact2(const PRec &r, int j, int jl, int u, const Sink &s, Acc &c,
-                                                     float eps2) {
+    __device__ static __forceinline__ float2 interact2(const PRec &r, int j, int jl, int u, const Sink &s, Acc &c,
+                                                       float eps2) {
         const float2 dx = add2(sub2(make_float2(r.w0.x, r.w0.y), s.xh), sub2(make_float2(r.w2.x, r.w2.y), s.xl));
         const float2 dy = add2(sub2(make_float2(r.w0.z, r.w0.w), s.yh), sub2(make_float2(r.w2.z, r.w2.w), s.yl));
         const float2 dz = add2(sub2(make_float2(r.w1.x, r.w1.y), s.zh), sub2(r.w3, s.zl));
@@ -444,6 +445,7 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
                 (SELF && j + jl == s.slot) ? 0xffffffffu : ((__float_as_uint(d2.y) & ~kKeyMask) | unsigned(u + 1));
             c.ck = FIRST ? min(ka, kb) : min(c.ck, min(ka, kb));
         }
+        return d2;
     }
     // End of a chunk whose pair records start at pq (pair stride pstep).  When
     // the chunk holds a new nearest neighbour, its exact r^2 (the operations
@@ -562,8 +564,9 @@ struct Fp64Force {
         c.nn_d2 = d_inf();
         c.nn_id = -1;
     }
+    // Returns the pair's unsoftened r^2 (used by the neighbour-list policy).
     template <bool SELF, bool FIRST>
-    __device__ static __forceinline__ void interact(const Rec &r, int j, int, const Sink &s, Acc &c, double eps2) {
+    __device__ static __forceinline__ double interact(const Rec &r, int j, int, const Sink &s, Acc &c, double eps2) {
         const double dx = r.w[0].x - s.x, dy = r.w[0].y - s.y, dz = r.w[1].x - s.z;
         const double m = r.w[1].y;
         const double dvx = r.w[2].x - s.vx, dvy = r.w[2].y - s.vy, dvz = r.w[3].x - s.vz;
@@ -599,6 +602,7 @@ struct Fp64Force {
                 c.nn_id = id;
             }
         }
+        return d2;
     }
     __device__ static __forceinline__ void fold(Acc &, int) {}
     __device__ static __forceinline__ void flush(Acc &, double *, int) {}
@@ -620,6 +624,57 @@ struct Fp64Force {
         MixedForce<ORDER, NN>::write_final(o, i, t, d, id);
     }
 };
+
+// ---------------------------------------------------------------------------
+// Neighbour lists (Sec. 1 and Sec. 3: the list of all particles within a
+// given radius of each sink, for perturber lists).  Wraps a force policy: after
+// each interaction, a source whose unsoftened r^2 is below the sink's h^2
+// (strictly; the self pair excluded) is appended to the sink's list by slot,
+// with one atomic per neighbour; slots beyond the capacity are counted but not
+// stored.  r^2 is the policy's own (FP32 double-single difference in mixed
+// precision, exact FP64 otherwise).  The lists are mapped to ids and sorted
+// after the pass.
+// ---------------------------------------------------------------------------
+template <class B>
+struct WithNeighbours : B {
+    static constexpr bool kNB = true;
+    typedef typename B::real real;
+    struct Sink : B::Sink {
+        real h2;       // squared radius; negative for an unused sink slot
+        int32_t *cnt;  // this sink's counter and list
+        int32_t *lst;
+        int cap;
+    };
+    __device__ static __forceinline__ void set_nb(Sink &s, const ForceParams &p, int64_t i, bool valid) {
+        s.h2 = valid ? static_cast<real>(p.nb_h2[i]) : static_cast<real>(-1);
+        s.cnt = p.nb_count + (valid ? i : 0);
+        s.lst = p.nb_list + (valid ? i : 0) * static_cast<int64_t>(p.nb_max);
+        s.cap = p.nb_max;
+    }
+    __device__ static __forceinline__ void add(const Sink &s, int j) {
+        const int k = atomicAdd(s.cnt, 1);
+        if (k < s.cap) s.lst[k] = j;
+    }
+    template <bool SELF, bool FIRST, class R>
+    __device__ static __forceinline__ float2 interact2(const R &r, int j, int jl, int u, const Sink &s,
+                                                       typename B::Acc &c, float eps2) {
+        const float2 d2 = B::template interact2<SELF, FIRST>(r, j, jl, u, s, c, eps2);
+        if (d2.x < s.h2 && (!SELF || j != s.slot)) add(s, j);
+        if (d2.y < s.h2 && (!SELF || j + jl != s.slot)) add(s, j + jl);
+        return d2;
+    }
+    template <bool SELF, bool FIRST, class R>
+    __device__ static __forceinline__ double interact(const R &r, int j, int u, const Sink &s, typename B::Acc &c,
+                                                      double eps2) {
+        const double d2 = B::template interact<SELF, FIRST>(r, j, u, s, c, eps2);
+        if (d2 < s.h2 && (!SELF || j != s.slot)) add(s, j);
+        return d2;
+    }
+};
+template <class P, class = void>
+struct is_nb { static constexpr bool value = false; };
+template <class P>
+struct is_nb<P, decltype(void(P::kNB))> { static constexpr bool value = P::kNB; };
 
 // ---------------------------------------------------------------------------
 // Adjoint policies.  For a pair (sink k, source l) with r = x_l - x_k,
@@ -1230,6 +1285,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             if constexpr (FUSED && P::kCanFuse) P::sink_from(P::predict(p.dsc, slot, p.t_hi, p.t_lo), sk[k]);
             else P::load_sink(p.rec, slot, sk[k]);
             sk[k].slot = val[k] ? slot : -1;
+            if constexpr (is_nb<P>::value) P::set_nb(sk[k], p, ii[k], val[k]);
             P::init(ac[k]);
             P::zero_totals(tot + k * P::NS * nt, nt);
         }
@@ -1590,6 +1646,19 @@ inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int gri
     return dispatch_ipt_f<P, false>(occ, ipt, p, grid, threads, tile, s, blocks);
 }
 
+// Neighbour-list kernels exist for one sink per thread only.
+template <class P>
+inline cudaError_t dispatch_nb(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
+                               cudaStream_t s, int *blocks, int fused) {
+    if (ipt != 1) return cudaErrorInvalidValue;
+    if constexpr (P::kCanFuse && is_paired<P>::value) {
+        if (fused) return occ ? occupancy_pass<P, 1, true>(threads, tile, blocks) : launch_pass<P, 1, true>(*p, grid, threads, tile, s);
+    } else {
+        if (fused) return cudaErrorInvalidValue;
+    }
+    return occ ? occupancy_pass<P, 1, false>(threads, tile, blocks) : launch_pass<P, 1, false>(*p, grid, threads, tile, s);
+}
+
 template <class P>
 inline cudaError_t launch_reduce(const ReduceParams &r, cudaStream_t s) {
     const int threads = 256;
@@ -1629,12 +1698,20 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
     namespace sp2 {                                                                                        \
     cudaError_t launch_force_##SUFFIX(const KernelKey &k, const ForceParams &p, int grid, int threads,     \
                                       size_t tile, cudaStream_t s) {                                       \
+        if (k.nb)                                                                                          \
+            return k.nn ? dispatch_nb<WithNeighbours<POLICY<ORDER, true>>>(false, k.ipt, &p, grid, threads,  \
+                                                                           tile, s, nullptr, k.fused)      \
+                        : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, tile, s, nullptr,  \
                                                         k.fused)                                           \
                     : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, tile, s, nullptr, \
                                                          k.fused);                                         \
     }                                                                                                      \
     cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t tile, int *blocks) {       \
+        if (k.nb)                                                                                          \
+            return k.nn ? dispatch_nb<WithNeighbours<POLICY<ORDER, true>>>(true, k.ipt, nullptr, 0, threads, \
+                                                                           tile, 0, blocks, k.fused)       \
+                        : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks,  \
                                                         k.fused)                                           \
                     : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks, \

@@ -76,6 +76,13 @@ struct ForceParams {
     // CTA) sums the i-block's partials in slice order and writes the outputs
     int fused_reduce;
     unsigned int *done;
+    // neighbour lists (kernels of the neighbour-list policy only): per sink
+    // position i, squared radius nb_h2[i], counter nb_count[i] (zero at launch)
+    // and nb_max slots at nb_list + i * nb_max
+    const double *nb_h2;
+    int32_t *nb_count;
+    int32_t *nb_list;
+    int nb_max;
     // VJP outputs / flags
     double *xbar, *vbar, *mbar;
     int accumulate;
@@ -124,6 +131,7 @@ struct KernelKey {
     int nn;     // 0 / 1
     int ipt;    // 1 / 2 / 4
     int fused;  // 1: predict sources in the pass (mixed force only)
+    int nb;     // 1: neighbour lists (force kernels with nearest neighbour, ipt 1)
 };
 
 // Each kernel translation unit provides these for its (order, precision).
@@ -169,6 +177,8 @@ cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n
 cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const double *x,
                               const double *v, unsigned char *rec, cudaStream_t s);
 cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
+cudaError_t launch_nb_finish(const int32_t *ids, int64_t n_i, int nb_max, const int32_t *count, int32_t *list,
+                             cudaStream_t s);
 cudaError_t launch_h4_predict_pack(int mixed, int64_t n, double dt, const double *m,
                                    const double *x, const double *v, const double *a,
                                    const double *jk, unsigned char *rec, cudaStream_t s);

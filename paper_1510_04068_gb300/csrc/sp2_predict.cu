@@ -166,6 +166,25 @@ __global__ void pack_state_kernel(int64_t n, const double *m, const double *x, c
     else store_fp64(rec, 64, j, xp, vp, nullptr, m[j], static_cast<int>(j));
 }
 
+// Neighbour lists after the pass: stored slots become ids and each list is
+// sorted by id (insertion sort; lists are short), so a list without overflow
+// has one defined order.
+__global__ void nb_finish_kernel(const int32_t *ids, int64_t n_i, int nb_max, const int32_t *count, int32_t *list) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_i) return;
+    const int c = min(count[i], nb_max);
+    int32_t *l = list + i * nb_max;
+    for (int k = 0; k < c; ++k) {
+        const int32_t v = ids[l[k]];
+        int q = k;
+        while (q > 0 && l[q - 1] > v) {
+            l[q] = l[q - 1];
+            --q;
+        }
+        l[q] = v;
+    }
+}
+
 __global__ void iota_kernel(int32_t *dst, int64_t n) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j < n) dst[j] = static_cast<int32_t>(j);
@@ -332,6 +351,13 @@ cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const doubl
 cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     iota_kernel<<<grid_for(n), kThreads, 0, s>>>(dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nb_finish(const int32_t *ids, int64_t n_i, int nb_max, const int32_t *count, int32_t *list,
+                             cudaStream_t s) {
+    if (n_i <= 0) return cudaSuccess;
+    nb_finish_kernel<<<grid_for(n_i), kThreads, 0, s>>>(ids, n_i, nb_max, count, list);
     return cudaGetLastError();
 }
 

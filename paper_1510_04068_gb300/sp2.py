@@ -10,7 +10,7 @@ in libsapporo_gb.so; if the library cannot be loaded, every call raises.
 from __future__ import annotations
 
 import ctypes
-from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_int, c_int64, c_size_t, c_void_p
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
 from pathlib import Path
 
 import numpy as np
@@ -59,6 +59,7 @@ _SIGS = [
     ("sp2_predict", [_P, c_double], c_int),
     ("sp2_compute", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_compute_range", [_P, c_int64, c_int64, c_int64, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
+    ("sp2_compute_nb", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P, c_int32, _P, _P, c_int], c_int),
     ("sp2_batch_plan_create", [_P, c_int64, _P, POINTER(_P)], c_int),
     ("sp2_batch_plan_destroy", [_P], c_int),
     ("sp2_compute_batched", [_P, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
@@ -189,6 +190,17 @@ def sp2_compute(ctx, i_idx, acc=None, jerk=None, snap=None, pot=None, nn_id=None
         _check(load().sp2_compute(ctx, len(i_idx), *ptrs, kind), ctx)
     else:
         _check(load().sp2_compute_range(ctx, int(j_range[0]), int(j_range[1]), len(i_idx), *ptrs, kind), ctx)
+
+
+def sp2_compute_nb(ctx, i_idx, h2, nb_max, nb_count, nb_ids, acc=None, jerk=None, snap=None, pot=None, nn_id=None,
+                   nn_r2=None):
+    """Forces plus neighbour lists: nb_count[k] neighbours of sink k within
+    sqrt(h2[k]); nb_ids[k, :min(nb_count[k], nb_max)] their ids, ascending."""
+    ptrs, kind, _k = _marshal([i_idx, acc, jerk, snap, pot, nn_id, nn_r2, h2, nb_count, nb_ids],
+                              [I4, F8, F8, F8, F8, I4, F8, F8, I4, I4])
+    pi, pa, pj, ps, pp, pid, pr2, ph2, pcnt, pids = ptrs
+    _check(load().sp2_compute_nb(ctx, len(i_idx), pi, pa, pj, ps, pp, pid, pr2, ph2, int(nb_max), pcnt, pids, kind),
+           ctx)
 
 
 def sp2_batch_plan_create(ctx, offsets):
@@ -337,6 +349,7 @@ class Context:
     def set_j(self, *a, **k): return sp2_set_j(self.ctx, *a, **k)
     def predict(self, t): return sp2_predict(self.ctx, t)
     def compute(self, *a, **k): return sp2_compute(self.ctx, *a, **k)
+    def compute_nb(self, *a, **k): return sp2_compute_nb(self.ctx, *a, **k)
     def batch_plan(self, offsets): return sp2_batch_plan_create(self.ctx, offsets)
     def compute_batched(self, *a, **k): return sp2_compute_batched(self.ctx, *a, **k)
     def forces(self, *a, **k): return sp2_forces(self.ctx, *a, **k)
