@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--n", type=int, default=131072)
     p.add_argument("--n-active", type=int, default=131072)
     p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint / lists lines")
-    p.add_argument("--extras", default="sweep,h6,batched,adjoint,nb",
+    p.add_argument("--extras", default="sweep,h6,batched,adjoint,nb,h2",
                    help="comma-separated secondary sections to run: sweep, h6, batched, adjoint")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -422,6 +422,8 @@ def extras(sp2, w, n, eps2, dev, stream, sections):
             res["adjoint"] = bench_adjoint(dev, stream)
         if "nb" in sections:
             res["nb"] = bench_nb(sp2, dev, stream)
+        if "h2" in sections:
+            res["h2"] = bench_h2(sp2, dev, stream)
     return res
 
 
@@ -554,6 +556,45 @@ def bench_nb(sp2, dev, stream):
                      "mean_neighbours": float(cc.mean()), "max_neighbours": int(cc.max()),
                      "overflowed": int((cc > 256).sum())})
     c.close()
+    return rows
+
+
+# FP32 FMA-pipe lane-operations of a leap-frog (order 2) interaction: 9 double-
+# single difference, 3 r^2, 1 softening add, 4 (rinv^2, m rinv, m rinv^3,
+# potential sum), 3 acc.
+OPS_PER_INTERACTION_H2 = 20
+
+
+def bench_h2(sp2, dev, stream):
+    """Leap-frog / GRAPE-5 pass (order 2: acc + pot + NN of sources at their
+    stored positions), Plummer N = 131072: mixed at N_active = 131072 and
+    16384, FP64 at 16384."""
+    import torch
+    n = 131072
+    m, x, _ = W.plummer(n, 0)
+    ids = W.particle_ids(n)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * peaks().get("sm_max_mhz", 2070.0) * 1e6
+    rows = []
+    for prec, name, actives in ((sp2.SP2_MIXED, "mixed", (131072, 16384)), (sp2.SP2_FP64, "fp64", (16384,))):
+        c = sp2.Context(order=2, precision=prec, n_max=n, eps2=1e-8, cuda_stream=stream.cuda_stream)
+        c.set_j(0, D(ids), D(m), D(x), None, None, None, None, None)
+        c.predict(0.0)
+        for na in actives:
+            idx = D(W.active_set(n, na, 4000 + na)) if na < n else D(np.arange(n, dtype=np.int32))
+            o = dict(acc=torch.empty((na, 3), dtype=torch.float64, device=dev),
+                     pot=torch.empty(na, dtype=torch.float64, device=dev),
+                     nn_id=torch.empty(na, dtype=torch.int32, device=dev),
+                     nn_r2=torch.empty(na, dtype=torch.float64, device=dev))
+            c.autotune(na)
+            ms = timed(lambda: (c.predict(0.0), c.compute(idx, **o)), 3 if name == "fp64" else 10, stream)
+            rate = na * n / (ms / 1e3)
+            row = {"precision": name, "n_active": na, "us_per_step": 1e3 * ms, "interactions_per_s": rate}
+            if name == "mixed":
+                row["fma_pipe_frac"] = rate * OPS_PER_INTERACTION_H2 / peak
+            rows.append(row)
+        c.close()
     return rows
 
 

@@ -69,7 +69,9 @@ typedef void *(*sp2_alloc_fn)(size_t bytes, void *user);
 typedef void (*sp2_free_fn)(void *ptr, void *user);
 
 typedef struct {
-    int order;            /* 4 (Hermite-4: acc, jerk, pot) or 6 (adds snap)            */
+    int order;            /* 4 (Hermite-4: acc, jerk, pot), 6 (adds snap), or 2        */
+                          /* (leap-frog / GRAPE-5 of Sec. 1: acc and pot only; sources */
+                          /* are used at their stored positions, not predicted)        */
     int precision;        /* SP2_FP64 or SP2_MIXED                                     */
     int64_t n_max;        /* capacity: number of j-particle slots                      */
     double eps2;          /* softening length squared, >= 0                            */
@@ -100,7 +102,7 @@ void sp2_config_default(sp2_config *cfg);
 
 /* Create a context on the current CUDA device (Sec. 2.2: one particle store and
  * its kernels per device).  Allocates the j store for cfg->n_max particles.
- * Errors: SP2_ERR_ARG (order not 4/6, precision, n_max <= 0 or > 2^30,
+ * Errors: SP2_ERR_ARG (order not 2/4/6, precision, n_max <= 0 or > 2^30,
  * eps2 < 0 or not finite, alloc without free), SP2_ERR_NOMEM, SP2_ERR_CUDA. */
 sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg);
 
@@ -115,7 +117,8 @@ sp2_status sp2_close(sp2_ctx *ctx);
  *                 `first` is ignored); used to update the active particles of a
  *                 block step.
  * id[n] int32, m[n], x/v/a/jerk[n x 3], snap[n x 3] (order 6 only, else NULL),
- * t[n] (time at which x, v, a, jerk, snap are valid).  Marks the predicted
+ * t[n] (time at which x, v, a, jerk, snap are valid).  Order 2 needs only id,
+ * m and x (v, a, jerk, t may be NULL: they are not used).  Marks the predicted
  * records stale.  Errors: SP2_ERR_ARG, SP2_ERR_RANGE. */
 sp2_status sp2_set_j(sp2_ctx *ctx, int64_t first, int64_t n, const int32_t *slots,
                      const int32_t *id, const double *m, const double *x, const double *v,
@@ -130,21 +133,24 @@ sp2_status sp2_set_j(sp2_ctx *ctx, int64_t first, int64_t n, const int32_t *slot
  * the polynomial in double-single arithmetic from a double-single copy of the
  * store, and defers the work: the next sp2_compute with few enough sinks
  * predicts its sources inside the force pass, any other consumer writes the
- * records first.  Results do not depend on which happens.
+ * records first.  Results do not depend on which happens.  Order 2 (leap-frog)
+ * takes the stored positions as they are.
  * Errors: SP2_ERR_STATE (nothing loaded), SP2_ERR_ARG (t not finite). */
 sp2_status sp2_predict(sp2_ctx *ctx, double t);
 
 /* Gravity kernel (Sec. 2.1 and 2.2.4): for each of the n_i sinks, given as
  * slots i_idx[n_i] (int32) of the loaded set, sum over the sources in slots
  * j_begin .. j_end-1 (sp2_compute: all loaded) except itself:
- *   acc[n_i x 3], jerk[n_i x 3], snap[n_i x 3] (order 6; else pass NULL),
+ *   acc[n_i x 3], jerk[n_i x 3] (order 4 and 6; NULL for order 2),
+ *   snap[n_i x 3] (order 6; else pass NULL),
  *   pot[n_i], nn_id[n_i] (int32, -1 when there is no other source),
  *   nn_r2[n_i] (unsoftened squared distance, +inf when none).
  * Any output may be NULL (not computed / not written); nn_* need with_nn.
  * Sinks are the predicted j-particles at t.  The source range is split into
  * slices over the whole GPU when n_i is small (Sec. 2.1, the source-split
  * method), and the slices are combined by a deterministic FP64 reduction
- * kernel.  Errors: SP2_ERR_STATE (records stale: call sp2_predict),
+ * (inside the force kernel, or a second kernel for large slice counts).
+ * Errors: SP2_ERR_STATE (records stale: call sp2_predict),
  * SP2_ERR_RANGE (slot >= loaded count, bad range), SP2_ERR_ARG,
  * SP2_ERR_NONFINITE (check_finite). n_i == 0 is a successful no-op. */
 sp2_status sp2_compute(sp2_ctx *ctx, int64_t n_i, const int32_t *i_idx,

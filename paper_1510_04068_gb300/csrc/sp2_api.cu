@@ -260,7 +260,7 @@ struct PassOut {
 size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
     const size_t ring = fused ? 0 : static_cast<size_t>(kStagesDevice) * tile * rb;
     const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
-    const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
+    const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
     return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);
 }
 
@@ -294,7 +294,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
-    const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : 7);
+    const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
     const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused);
     if (smem_total > 200 * 1024)
         return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max 200 KiB)", smem_total);
@@ -479,29 +479,35 @@ cudaError_t launch_force_kernel(const KernelKey &k, const ForceParams &p, int gr
                                         : launch_force_vjpd(k, p, grid, threads, tile, s);
     if (k.order == 6) return k.mixed ? launch_force_h6m(k, p, grid, threads, tile, s)
                                      : launch_force_h6d(k, p, grid, threads, tile, s);
+    if (k.order == 2) return k.mixed ? launch_force_h2m(k, p, grid, threads, tile, s)
+                                     : launch_force_h2d(k, p, grid, threads, tile, s);
     return k.mixed ? launch_force_h4m(k, p, grid, threads, tile, s) : launch_force_h4d(k, p, grid, threads, tile, s);
 }
 
 cudaError_t force_kernel_occupancy(const KernelKey &k, int threads, size_t tile, int *b) {
     if (k.kind == K_VJP) return k.mixed ? occupancy_force_vjpm(k, threads, tile, b) : occupancy_force_vjpd(k, threads, tile, b);
     if (k.order == 6) return k.mixed ? occupancy_force_h6m(k, threads, tile, b) : occupancy_force_h6d(k, threads, tile, b);
+    if (k.order == 2) return k.mixed ? occupancy_force_h2m(k, threads, tile, b) : occupancy_force_h2d(k, threads, tile, b);
     return k.mixed ? occupancy_force_h4m(k, threads, tile, b) : occupancy_force_h4d(k, threads, tile, b);
 }
 
 cudaError_t launch_reduce_kernel(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {
     if (k.kind == K_VJP) return k.mixed ? launch_reduce_vjpm(k, r, s) : launch_reduce_vjpd(k, r, s);
     if (k.order == 6) return k.mixed ? launch_reduce_h6m(k, r, s) : launch_reduce_h6d(k, r, s);
+    if (k.order == 2) return k.mixed ? launch_reduce_h2m(k, r, s) : launch_reduce_h2d(k, r, s);
     return k.mixed ? launch_reduce_h4m(k, r, s) : launch_reduce_h4d(k, r, s);
 }
 
 cudaError_t launch_batched_kernel(int order, int mixed, int nn, const BatchParams &b, int grid, int threads,
                                   cudaStream_t s) {
     if (order == 6) return mixed ? launch_batched_h6m(nn, b, grid, threads, s) : launch_batched_h6d(nn, b, grid, threads, s);
+    if (order == 2) return mixed ? launch_batched_h2m(nn, b, grid, threads, s) : launch_batched_h2d(nn, b, grid, threads, s);
     return mixed ? launch_batched_h4m(nn, b, grid, threads, s) : launch_batched_h4d(nn, b, grid, threads, s);
 }
 
 cudaError_t batched_kernel_occupancy(int order, int mixed, int nn, int threads, int *b) {
     if (order == 6) return mixed ? occupancy_batched_h6m(nn, threads, b) : occupancy_batched_h6d(nn, threads, b);
+    if (order == 2) return mixed ? occupancy_batched_h2m(nn, threads, b) : occupancy_batched_h2d(nn, threads, b);
     return mixed ? occupancy_batched_h4m(nn, threads, b) : occupancy_batched_h4d(nn, threads, b);
 }
 
@@ -541,7 +547,7 @@ sp2_status sp2_last_error(const sp2_ctx *ctx, char *buf, size_t len) {
 sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg) {
     if (!out || !cfg) return SP2_ERR_ARG;
     *out = nullptr;
-    if (cfg->order != 4 && cfg->order != 6) return SP2_ERR_ARG;
+    if (cfg->order != 2 && cfg->order != 4 && cfg->order != 6) return SP2_ERR_ARG;
     if (cfg->precision != SP2_FP64 && cfg->precision != SP2_MIXED) return SP2_ERR_ARG;
     if (cfg->n_max <= 0 || cfg->n_max > (int64_t(1) << 30)) return SP2_ERR_ARG;
     if (!(cfg->eps2 >= 0.0) || !std::isfinite(cfg->eps2)) return SP2_ERR_ARG;
@@ -570,7 +576,7 @@ sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg) {
     c->tmp = static_cast<double *>(dalloc(c, 4 * n3));
     c->dev_words = static_cast<unsigned int *>(dalloc(c, 64));
     const bool ok = c->js.id && c->js.m && c->js.t && c->js.x && c->js.v && c->js.a && c->js.jk &&
-                    (cfg->order == 4 || c->js.sn) && (!mixed || c->js.dsc) && c->rec && c->rec2 && c->iota &&
+                    (cfg->order != 6 || c->js.sn) && (!mixed || c->js.dsc) && c->rec && c->rec2 && c->iota &&
                     c->tmp && c->dev_words;
     if (!ok) {
         while (!c->owned.empty()) dfree(c, c->owned.back());
@@ -588,6 +594,11 @@ sp2_status sp2_open(sp2_ctx **out, const sp2_config *cfg) {
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_words, 0, 64, c->stream);
+    if (cfg->order == 2) {  // velocities, accelerations, jerks and times are optional inputs
+        for (double *q : {c->js.v, c->js.a, c->js.jk})
+            if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, n3, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->js.t, 0, n * sizeof(double), c->stream);
+    }
     if (e == cudaSuccess) e = launch_iota(c->iota, cfg->n_max, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -628,9 +639,10 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
     SP2_CKS(check_ptr_kind(c, ptr_kind));
     if (n < 0) return fail(c, SP2_ERR_ARG, "n < 0");
     if (n == 0) return SP2_OK;
-    if (!id || !m || !x || !v || !a || !jerk || !t) return fail(c, SP2_ERR_ARG, "null input array");
+    if (!id || !m || !x) return fail(c, SP2_ERR_ARG, "null input array");
+    if (c->cfg.order != 2 && (!v || !a || !jerk || !t)) return fail(c, SP2_ERR_ARG, "null input array");
     if (c->cfg.order == 6 && !snap) return fail(c, SP2_ERR_ARG, "order 6 needs snap");
-    if (c->cfg.order == 4 && snap) return fail(c, SP2_ERR_ARG, "snap must be NULL for order 4");
+    if (c->cfg.order != 6 && snap) return fail(c, SP2_ERR_ARG, "snap must be NULL below order 6");
     if (!slots) {
         if (first < 0 || first + n > c->cfg.n_max) return fail(c, SP2_ERR_RANGE, "slots [%lld, %lld) exceed n_max %lld",
                                                                  (long long)first, (long long)(first + n), (long long)c->cfg.n_max);
@@ -650,11 +662,11 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
             const size_t o = static_cast<size_t>(first);
             SP2_CK(c, cudaMemcpyAsync(c->js.id + o, id, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
             SP2_CK(c, cudaMemcpyAsync(c->js.m + o, m, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.t + o, t, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            if (t) SP2_CK(c, cudaMemcpyAsync(c->js.t + o, t, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
             SP2_CK(c, cudaMemcpyAsync(c->js.x + 3 * o, x, n3, cudaMemcpyHostToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.v + 3 * o, v, n3, cudaMemcpyHostToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.a + 3 * o, a, n3, cudaMemcpyHostToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.jk + 3 * o, jerk, n3, cudaMemcpyHostToDevice, c->stream));
+            if (v) SP2_CK(c, cudaMemcpyAsync(c->js.v + 3 * o, v, n3, cudaMemcpyHostToDevice, c->stream));
+            if (a) SP2_CK(c, cudaMemcpyAsync(c->js.a + 3 * o, a, n3, cudaMemcpyHostToDevice, c->stream));
+            if (jerk) SP2_CK(c, cudaMemcpyAsync(c->js.jk + 3 * o, jerk, n3, cudaMemcpyHostToDevice, c->stream));
             if (snap) SP2_CK(c, cudaMemcpyAsync(c->js.sn + 3 * o, snap, n3, cudaMemcpyHostToDevice, c->stream));
             if (c->js.dsc) {
                 ev_begin(c, ST_OTHER);
@@ -685,11 +697,11 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
             const size_t o = static_cast<size_t>(first);
             SP2_CK(c, cudaMemcpyAsync(c->js.id + o, id, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
             SP2_CK(c, cudaMemcpyAsync(c->js.m + o, m, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.t + o, t, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            if (t) SP2_CK(c, cudaMemcpyAsync(c->js.t + o, t, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
             SP2_CK(c, cudaMemcpyAsync(c->js.x + 3 * o, x, n3, cudaMemcpyDeviceToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.v + 3 * o, v, n3, cudaMemcpyDeviceToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.a + 3 * o, a, n3, cudaMemcpyDeviceToDevice, c->stream));
-            SP2_CK(c, cudaMemcpyAsync(c->js.jk + 3 * o, jerk, n3, cudaMemcpyDeviceToDevice, c->stream));
+            if (v) SP2_CK(c, cudaMemcpyAsync(c->js.v + 3 * o, v, n3, cudaMemcpyDeviceToDevice, c->stream));
+            if (a) SP2_CK(c, cudaMemcpyAsync(c->js.a + 3 * o, a, n3, cudaMemcpyDeviceToDevice, c->stream));
+            if (jerk) SP2_CK(c, cudaMemcpyAsync(c->js.jk + 3 * o, jerk, n3, cudaMemcpyDeviceToDevice, c->stream));
             if (snap) SP2_CK(c, cudaMemcpyAsync(c->js.sn + 3 * o, snap, n3, cudaMemcpyDeviceToDevice, c->stream));
             if (c->js.dsc) {
                 ev_begin(c, ST_OTHER);
@@ -743,7 +755,8 @@ static sp2_status compute_impl(sp2_ctx *c, int64_t j_begin, int64_t j_end, int64
         return fail(c, SP2_ERR_RANGE, "source range [%lld, %lld) outside the loaded set [0, %lld)", (long long)j_begin,
                     (long long)j_end, (long long)c->n_loaded);
     if (n_i > (int64_t(1) << 30)) return fail(c, SP2_ERR_RANGE, "n_i too large");
-    if (snap && c->cfg.order != 6) return fail(c, SP2_ERR_ARG, "snap requested from an order-4 context");
+    if (snap && c->cfg.order != 6) return fail(c, SP2_ERR_ARG, "snap requested from a context below order 6");
+    if (jerk && c->cfg.order == 2) return fail(c, SP2_ERR_ARG, "jerk requested from an order-2 (leap-frog) context");
     if ((nn_id || nn_r2) && !c->cfg.with_nn) return fail(c, SP2_ERR_UNSUPPORTED, "context opened without nearest neighbour");
     const bool want_nb = h2 || nb_count || nb_ids;
     if (want_nb) {
@@ -880,7 +893,8 @@ sp2_status sp2_compute_batched(sp2_ctx *c, const sp2_batch_plan *plan, double *a
     SP2_CKS(check_ptr_kind(c, ptr_kind));
     if (!plan || plan->ctx != c) return fail(c, SP2_ERR_ARG, "plan does not belong to this context");
     if (!c->rec_valid) return fail(c, SP2_ERR_STATE, "predicted records are stale: call sp2_predict first");
-    if (snap && c->cfg.order != 6) return fail(c, SP2_ERR_ARG, "snap requested from an order-4 context");
+    if (snap && c->cfg.order != 6) return fail(c, SP2_ERR_ARG, "snap requested from a context below order 6");
+    if (jerk && c->cfg.order == 2) return fail(c, SP2_ERR_ARG, "jerk requested from an order-2 (leap-frog) context");
     if ((nn_id || nn_r2) && !c->cfg.with_nn) return fail(c, SP2_ERR_UNSUPPORTED, "context opened without nearest neighbour");
     if (plan->n_items == 0) return SP2_OK;
     if (plan->out_base + plan->n_rows > c->n_loaded) return fail(c, SP2_ERR_RANGE, "plan exceeds the loaded set");
@@ -1061,7 +1075,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     // scratch outputs in tmp (3 n_max doubles each suffice for acc/jerk/snap of n_i <= n_max)
     PassOut o;
     o.acc = c->tmp;
-    o.jerk = c->tmp + 3 * c->cfg.n_max;
+    o.jerk = order == 2 ? nullptr : c->tmp + 3 * c->cfg.n_max;
     o.snap = order == 6 ? c->tmp + 6 * c->cfg.n_max : nullptr;
     o.pot = c->tmp + 9 * c->cfg.n_max;
     o.nn_r2 = nn ? c->tmp + 9 * c->cfg.n_max + n_i : nullptr;

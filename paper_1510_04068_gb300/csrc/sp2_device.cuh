@@ -110,7 +110,7 @@ template <int ORDER, bool NN>
 struct MixedForce {
     static constexpr int NW = (ORDER == 6) ? 4 : 3;  // 16-byte words per record
     static constexpr int RB = NW * 16;
-    static constexpr int NS = (ORDER == 6) ? 10 : 7;  // summed fields
+    static constexpr int NS = (ORDER == 6) ? 10 : (ORDER == 2 ? 4 : 7);  // summed fields
     static constexpr bool kNN = NN;
     static constexpr bool kSmemTotals = true;
     static constexpr int kChunk = 8;
@@ -212,7 +212,11 @@ struct MixedForce {
         c.f[NS - 1] = FIRST ? mr : c.f[NS - 1] + mr;
         const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
         const float al3 = 3.f * (rv * rinv2);
-        if (ORDER == 4) {
+        if (ORDER == 2) {
+            c.f[0] = FIRST ? mr3 * dx : fmaf(mr3, dx, c.f[0]);
+            c.f[1] = FIRST ? mr3 * dy : fmaf(mr3, dy, c.f[1]);
+            c.f[2] = FIRST ? mr3 * dz : fmaf(mr3, dz, c.f[2]);
+        } else if (ORDER == 4) {
             c.f[0] = FIRST ? mr3 * dx : fmaf(mr3, dx, c.f[0]);
             c.f[1] = FIRST ? mr3 * dy : fmaf(mr3, dy, c.f[1]);
             c.f[2] = FIRST ? mr3 * dz : fmaf(mr3, dz, c.f[2]);
@@ -289,7 +293,7 @@ struct MixedForce {
     template <class Out>
     __device__ static __forceinline__ void write_final(const Out &o, int64_t i, const double *t, double d, int id) {
         if (o.acc) { o.acc[3 * i] = t[0]; o.acc[3 * i + 1] = t[1]; o.acc[3 * i + 2] = t[2]; }
-        if (o.jerk) { o.jerk[3 * i] = t[3]; o.jerk[3 * i + 1] = t[4]; o.jerk[3 * i + 2] = t[5]; }
+        if (ORDER != 2 && o.jerk) { o.jerk[3 * i] = t[3]; o.jerk[3 * i + 1] = t[4]; o.jerk[3 * i + 2] = t[5]; }
         if (ORDER == 6 && o.snap) { o.snap[3 * i] = t[6]; o.snap[3 * i + 1] = t[7]; o.snap[3 * i + 2] = t[8]; }
         if (o.pot) o.pot[i] = t[NS - 1];
         if (NN) {
@@ -407,7 +411,11 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
         const float2 rv = fma2(dz, dvz, fma2(dy, dvy, mul2(dx, dvx)));
         const float2 al = mul2(rv, rinv2);
         const float2 nal3 = mul2(dup2(-3.f), al);  // -alpha * 3 (sign folded into the constant)
-        if (ORDER == 4) {
+        if (ORDER == 2) {
+            c.f[0] = FIRST ? mul2(mr3, dx) : fma2(mr3, dx, c.f[0]);
+            c.f[1] = FIRST ? mul2(mr3, dy) : fma2(mr3, dy, c.f[1]);
+            c.f[2] = FIRST ? mul2(mr3, dz) : fma2(mr3, dz, c.f[2]);
+        } else if (ORDER == 4) {
             c.f[0] = FIRST ? mul2(mr3, dx) : fma2(mr3, dx, c.f[0]);
             c.f[1] = FIRST ? mul2(mr3, dy) : fma2(mr3, dy, c.f[1]);
             c.f[2] = FIRST ? mul2(mr3, dz) : fma2(mr3, dz, c.f[2]);
@@ -516,7 +524,7 @@ struct Fp64Force {
     static constexpr int NW = (ORDER == 6) ? 6 : 4;
     static constexpr bool kCanFuse = false;
     static constexpr int RB = NW * 16;
-    static constexpr int NS = (ORDER == 6) ? 10 : 7;
+    static constexpr int NS = (ORDER == 6) ? 10 : (ORDER == 2 ? 4 : 7);
     static constexpr bool kNN = NN;
     static constexpr bool kSmemTotals = false;
     static constexpr int kChunk = 8;
@@ -584,7 +592,7 @@ struct Fp64Force {
         const double Jy = mr3 * dvy - 3.0 * al * Ay;
         const double Jz = mr3 * dvz - 3.0 * al * Az;
         c.ax += Ax; c.ay += Ay; c.az += Az;
-        c.jx += Jx; c.jy += Jy; c.jz += Jz;
+        if (ORDER != 2) { c.jx += Jx; c.jy += Jy; c.jz += Jz; }
         if (ORDER == 6) {
             const double dax = r.w[4].x - s.ax, day = r.w[4].y - s.ay, daz = r.w[5].x - s.az;
             const double vv = dvx * dvx + dvy * dvy + dvz * dvz;
@@ -609,6 +617,7 @@ struct Fp64Force {
     __device__ static __forceinline__ void zero_totals(double *, int) {}
     __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
         t[0] = c.ax; t[1] = c.ay; t[2] = c.az;
+        if (ORDER == 2) { t[3] = c.pot; return; }
         t[3] = c.jx; t[4] = c.jy; t[5] = c.jz;
         if (ORDER == 6) { t[6] = c.sx; t[7] = c.sy; t[8] = c.sz; t[9] = c.pot; }
         else { t[6] = c.pot; }

@@ -54,6 +54,13 @@ template <int ORDER>
 __device__ __forceinline__ void predict_ds_record(const float4 *dsc, int64_t j, float t_hi, float t_lo, float4 *o) {
     constexpr int W = (ORDER == 6) ? 8 : 7;
     const float4 *q = dsc + j * W;
+    if (ORDER == 2) {  // leap-frog (GRAPE-5) sources are used where they are
+        const float4 w0 = q[0], w1 = q[1], w3 = q[3];
+        o[0] = w0;
+        o[1] = make_float4(w1.x, w1.y, w1.z, w3.w);
+        o[2] = o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const float4 w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4], w5 = q[5], w6 = q[6];
     float4 w7 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (ORDER == 6) w7 = q[7];

@@ -24,7 +24,8 @@ struct JStore {
 };
 __host__ __device__ constexpr int dscache_words(int order) { return order == 6 ? 8 : 7; }
 
-// Bytes of one predicted record.
+// Bytes of one predicted record (order 2, leap-frog: the order-4 layout with
+// zero velocities).
 //   mixed H4: {xh yh zh m}{xl yl zl id}{vx vy vz 0}            48 B
 //   mixed H6: + {ax ay az 0}                                   64 B
 //   fp64  H4: {x y}{z m}{vx vy}{vz id}                         64 B
@@ -153,6 +154,8 @@ cudaError_t batched_kernel_occupancy(int order, int mixed, int nn, int threads, 
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &, const ReduceParams &, cudaStream_t);     \
     cudaError_t launch_batched_##SUFFIX(int, const BatchParams &, int, int, cudaStream_t);         \
     cudaError_t occupancy_batched_##SUFFIX(int, int, int *);
+SP2_DECLARE_TU(h2m)
+SP2_DECLARE_TU(h2d)
 SP2_DECLARE_TU(h4m)
 SP2_DECLARE_TU(h4d)
 SP2_DECLARE_TU(h6m)

@@ -103,12 +103,12 @@ __global__ void scatter_kernel(JStore d, const int32_t *slots, int64_t n, int64_
     }
     d.id[s] = id[k];
     d.m[s] = m[k];
-    d.t[s] = t[k];
+    d.t[s] = t ? t[k] : 0.0;  // v, a, jk, t may be absent for leap-frog (order 2) sources
     for (int c = 0; c < 3; ++c) {
         d.x[3 * s + c] = x[3 * k + c];
-        d.v[3 * s + c] = v[3 * k + c];
-        d.a[3 * s + c] = a[3 * k + c];
-        d.jk[3 * s + c] = jk[3 * k + c];
+        d.v[3 * s + c] = v ? v[3 * k + c] : 0.0;
+        d.a[3 * s + c] = a ? a[3 * k + c] : 0.0;
+        d.jk[3 * s + c] = jk ? jk[3 * k + c] : 0.0;
         if (sn) d.sn[3 * s + c] = sn[3 * k + c];
     }
     if (d.dsc) write_dscache(d, s);
@@ -133,7 +133,10 @@ __global__ void predict_kernel(JStore js, int64_t n, double t, unsigned char *re
     for (int c = 0; c < 3; ++c) {
         const int64_t q = 3 * j + c;
         const double x = js.x[q], v = js.v[q], a = js.a[q], jk = js.jk[q];
-        if (MIXED && ORDER == 6) {
+        if (ORDER == 2) {  // leap-frog (GRAPE-5): sources are used where they are
+            xp[c] = x;
+            vp[c] = 0.0;
+        } else if (MIXED && ORDER == 6) {
             const double s = js.sn[q];
             xp[c] = fma(fma(fma(fma(s, d4, jk * (1.0 / 6.0)), dt, 0.5 * a), dt, v), dt, x);
             vp[c] = fma(fma(fma(s, d3, 0.5 * jk), dt, a), dt, v);
@@ -327,12 +330,16 @@ cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, do
         const float th = static_cast<float>(t);
         const float tl = static_cast<float>(t - static_cast<double>(th));
         if (order == 6) predict_ds_kernel<6><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
+        else if (order == 2) predict_ds_kernel<2><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
         else predict_ds_kernel<4><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
         return cudaGetLastError();
     }
     if (order == 6) {
         if (mixed) predict_kernel<6, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
         else predict_kernel<6, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
+    } else if (order == 2) {
+        if (mixed) predict_kernel<2, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
+        else predict_kernel<2, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
     } else {
         if (mixed) predict_kernel<4, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
         else predict_kernel<4, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
