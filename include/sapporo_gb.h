@@ -221,6 +221,42 @@ sp2_status sp2_force_vjp(sp2_ctx *ctx, int64_t n, const double *m, const double 
                          const double *pbar, double *xbar, double *vbar, double *mbar,
                          int accumulate, int ptr_kind);
 
+/* Read back loaded particles first .. first+n-1 from the store (any output may
+ * be NULL): x, v, a, jerk [n x 3] and t [n], as last set by sp2_set_j or
+ * advanced by sp2_block_run.  The paper has no counterpart (the integrator
+ * keeps its own copy of the particles).  Errors: SP2_ERR_RANGE. */
+sp2_status sp2_get_j(sp2_ctx *ctx, int64_t first, int64_t n, double *x, double *v,
+                     double *a, double *jerk, double *t, int ptr_kind);
+
+/* Block time-steps (Sec. 3.7: individual power-of-two time-steps; the paper
+ * leaves the integrator to the host, here it runs on the device around the
+ * force pass).  Order-4 contexts only.
+ * sp2_block_init: the loaded particles (x, v and m, with t = t0 for all) get
+ *   their acceleration and jerk at t0 from one full pass and initial steps
+ *   eta_s |a| / |j|, each the largest power of two not above that, dt_max at
+ *   most, dividing t0.
+ * sp2_block_run: repeat until the next block time exceeds t_end: the block
+ *   time t1 = min_i(t_i + dt_i), the active set {i : t_i + dt_i = t1}, the
+ *   prediction of all particles to t1, the force pass on the active set, and
+ *   the 4th-order Hermite corrector (Makino & Aarseth 1992) on it, followed by
+ *   Aarseth's time-step criterion with parameter eta (from the Hermite
+ *   interpolation of the step), quantised to a power of two at most twice
+ *   the last step and dt_max, dividing t1.  Afterwards every particle is at
+ *   its own t_i <= t_end (all at t_end when t_end is a multiple of dt_max).
+ *   Statistics go to *stats (may be NULL).
+ * Errors: SP2_ERR_UNSUPPORTED (order), SP2_ERR_STATE (nothing loaded, or
+ * block_run without block_init after the last sp2_set_j), SP2_ERR_ARG. */
+typedef struct {
+    int64_t block_steps;   /* force passes taken                          */
+    int64_t active_sum;    /* sum of N_active over the passes             */
+    int64_t max_active;
+    int64_t min_active;
+    double t;              /* time of the last block (-1 if none)         */
+} sp2_block_stats;
+sp2_status sp2_block_init(sp2_ctx *ctx, double t0, double eta_s, double dt_max);
+sp2_status sp2_block_run(sp2_ctx *ctx, double t_end, double eta, double dt_max,
+                         sp2_block_stats *stats);
+
 /* One shared time-step of the 4th-order Hermite scheme (Makino & Aarseth 1992)
  * on device arrays, in place: predict (x, v) with (a, jerk), evaluate acc and
  * jerk there (sp2_forces), correct

@@ -69,6 +69,10 @@ struct sp2_ctx {
     size_t part_cap = 0, part_id_cap = 0;   // bytes
     unsigned int *done = nullptr;           // per-i-block arrival counters of the fused reduction
     size_t done_cap = 0;                    // bytes
+    double *blk_dt = nullptr;               // block time-steps: per-slot step
+    int32_t *blk_active = nullptr;          // block time-steps: active slots
+    size_t blk_dt_cap = 0, blk_active_cap = 0;
+    bool blk_ready = false;                 // sp2_block_init has run since the last set_j
     unsigned char *stage = nullptr;  // staging for host-pointer calls
     size_t stage_cap = 0;
     std::vector<void *> owned;       // everything allocated (for close)
@@ -640,6 +644,7 @@ sp2_status sp2_set_j(sp2_ctx *c, int64_t first, int64_t n, const int32_t *slots,
     if (n < 0) return fail(c, SP2_ERR_ARG, "n < 0");
     if (n == 0) return SP2_OK;
     if (!id || !m || !x) return fail(c, SP2_ERR_ARG, "null input array");
+    c->blk_ready = false;
     if (c->cfg.order != 2 && (!v || !a || !jerk || !t)) return fail(c, SP2_ERR_ARG, "null input array");
     if (c->cfg.order == 6 && !snap) return fail(c, SP2_ERR_ARG, "order 6 needs snap");
     if (c->cfg.order != 6 && snap) return fail(c, SP2_ERR_ARG, "snap must be NULL below order 6");
@@ -1000,6 +1005,95 @@ sp2_status sp2_force_vjp(sp2_ctx *c, int64_t n, const double *m, const double *x
     c->launches += 1;
     SP2_CKS(run_pass(c, K_VJP, 4, mixed, 0, c->rec2, vjp_record_bytes(mixed), n, c->iota, n, 0, n, o, nullptr, ST_VJP));
     if (ptr_kind == SP2_HOST) SP2_CKS(stage_copy_out(s));
+    return SP2_OK;
+}
+
+sp2_status sp2_get_j(sp2_ctx *c, int64_t first, int64_t n, double *x, double *v, double *a, double *jerk, double *t,
+                     int ptr_kind) {
+    SP2_CKS(usable(c));
+    SP2_CKS(check_ptr_kind(c, ptr_kind));
+    if (n < 0 || first < 0 || first + n > c->n_loaded) return fail(c, SP2_ERR_RANGE, "slots outside the loaded set");
+    if (n == 0) return SP2_OK;
+    const cudaMemcpyKind k = ptr_kind == SP2_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double), o = static_cast<size_t>(first);
+    if (x) SP2_CK(c, cudaMemcpyAsync(x, c->js.x + 3 * o, n3, k, c->stream));
+    if (v) SP2_CK(c, cudaMemcpyAsync(v, c->js.v + 3 * o, n3, k, c->stream));
+    if (a) SP2_CK(c, cudaMemcpyAsync(a, c->js.a + 3 * o, n3, k, c->stream));
+    if (jerk) SP2_CK(c, cudaMemcpyAsync(jerk, c->js.jk + 3 * o, n3, k, c->stream));
+    if (t) SP2_CK(c, cudaMemcpyAsync(t, c->js.t + o, n * sizeof(double), k, c->stream));
+    if (ptr_kind == SP2_HOST) SP2_CK(c, cudaStreamSynchronize(c->stream));
+    return SP2_OK;
+}
+
+sp2_status sp2_block_init(sp2_ctx *c, double t0, double eta_s, double dt_max) {
+    SP2_CKS(usable(c));
+    if (c->cfg.order != 4) return fail(c, SP2_ERR_UNSUPPORTED, "block time-steps need an order-4 context");
+    if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
+    if (c->capturing) return fail(c, SP2_ERR_STATE, "cannot start block steps during graph capture");
+    if (!std::isfinite(t0) || !(eta_s > 0.0) || !(dt_max > 0.0) || !std::isfinite(dt_max))
+        return fail(c, SP2_ERR_ARG, "bad t0, eta_s or dt_max");
+    const int64_t n = c->n_loaded;
+    SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->blk_dt), &c->blk_dt_cap, n * sizeof(double), "block-step"));
+    SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->blk_active), &c->blk_active_cap, n * sizeof(int32_t), "block-step"));
+    // a and jerk of every particle at t0 (the stored times are taken to be t0)
+    SP2_CKS(sp2_predict(c, t0));
+    PassOut o;
+    o.acc = c->js.a;  // the pass reads the predicted records, not the store
+    o.jerk = c->js.jk;
+    SP2_CKS(materialize(c));
+    SP2_CKS(run_pass(c, K_FORCE, 4, c->cfg.precision == SP2_MIXED, 0, c->rec, c->rb, n, c->iota, n, 0, n, o, nullptr,
+                     ST_FORCE));
+    SP2_CK(c, launch_block_init(c->js, c->blk_dt, n, eta_s, dt_max, t0, c->stream));
+    if (c->js.dsc) SP2_CK(c, launch_dscache(c->cfg.order, c->js, 0, n, c->stream));
+    c->launches += 2;
+    c->rec_valid = false;
+    c->blk_ready = true;
+    SP2_CK(c, cudaStreamSynchronize(c->stream));
+    return SP2_OK;
+}
+
+sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp2_block_stats *st) {
+    SP2_CKS(usable(c));
+    if (!c->blk_ready) return fail(c, SP2_ERR_STATE, "call sp2_block_init first");
+    if (c->capturing) return fail(c, SP2_ERR_STATE, "cannot run block steps during graph capture");
+    if (!std::isfinite(t_end) || !(eta > 0.0) || !(dt_max > 0.0)) return fail(c, SP2_ERR_ARG, "bad t_end, eta or dt_max");
+    const int64_t n = c->n_loaded;
+    const int mixed = c->cfg.precision == SP2_MIXED;
+    double *a1 = c->tmp, *j1 = c->tmp + 3 * c->cfg.n_max;
+    unsigned int *count = c->dev_words + 6;
+    unsigned long long *t1bits = reinterpret_cast<unsigned long long *>(c->dev_words + 8);
+    sp2_block_stats acc{};
+    acc.min_active = INT64_MAX;
+    acc.t = -1.0;
+    for (;;) {
+        SP2_CK(c, launch_block_select(c->js.t, c->blk_dt, n, t1bits, c->blk_active, count, c->stream));
+        unsigned int hw[4];
+        SP2_CK(c, cudaMemcpyAsync(hw, c->dev_words + 6, sizeof hw, cudaMemcpyDeviceToHost, c->stream));
+        SP2_CK(c, cudaStreamSynchronize(c->stream));
+        c->launches += 2;
+        unsigned long long bits = static_cast<unsigned long long>(hw[2]) | (static_cast<unsigned long long>(hw[3]) << 32);
+        double t1;
+        std::memcpy(&t1, &bits, sizeof t1);
+        const int64_t n_act = hw[0];
+        if (!(t1 <= t_end) || n_act == 0) break;
+        SP2_CKS(sp2_predict(c, t1));
+        PassOut o;
+        o.acc = a1;
+        o.jerk = j1;
+        SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec, c->rb, n, c->blk_active, n_act, 0, n, o, nullptr, ST_FORCE,
+                         nullptr, true));
+        SP2_CK(c, launch_block_correct(c->js, c->blk_dt, c->blk_active, n_act, t1, a1, j1, eta, dt_max, c->stream));
+        c->launches += 1;
+        c->rec_valid = false;
+        acc.block_steps += 1;
+        acc.active_sum += n_act;
+        acc.max_active = std::max(acc.max_active, n_act);
+        acc.min_active = std::min(acc.min_active, n_act);
+        acc.t = t1;
+    }
+    SP2_CK(c, cudaStreamSynchronize(c->stream));
+    if (acc.block_steps == 0) acc.min_active = 0;
+    if (st) *st = acc;
     return SP2_OK;
 }
 

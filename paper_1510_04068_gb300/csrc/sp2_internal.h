@@ -180,6 +180,14 @@ cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n
 cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const double *x,
                               const double *v, unsigned char *rec, cudaStream_t s);
 cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
+// Block time-steps (Hermite-4 with individual power-of-two steps).
+cudaError_t launch_block_init(const JStore &js, double *dt, int64_t n, double eta_s, double dt_max, double t0,
+                              cudaStream_t s);
+// *t1bits = bits of min(t + dt); active[0 .. *count) = slots with t + dt == t1
+cudaError_t launch_block_select(const double *t, const double *dt, int64_t n, unsigned long long *t1bits,
+                                int32_t *active, unsigned int *count, cudaStream_t s);
+cudaError_t launch_block_correct(const JStore &js, double *dt, const int32_t *active, int64_t n_act, double t1,
+                                 const double *a1, const double *j1, double eta, double dt_max, cudaStream_t s);
 cudaError_t launch_nb_finish(const int32_t *ids, int64_t n_i, int nb_max, const int32_t *count, int32_t *list,
                              cudaStream_t s);
 cudaError_t launch_h4_predict_pack(int mixed, int64_t n, double dt, const double *m,

@@ -18,6 +18,7 @@ namespace sp2 {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr double kBlockDtMin = 1.0 / (1ll << 50);  // smallest block step (2^-50)
 
 inline unsigned grid_for(int64_t n) { return static_cast<unsigned>((n + kThreads - 1) / kThreads); }
 
@@ -186,6 +187,90 @@ __global__ void nb_finish_kernel(const int32_t *ids, int64_t n_i, int nb_max, co
         }
         l[q] = v;
     }
+}
+
+// ---- block time-steps (Sec. 3.7: Hermite integration with individual,
+// power-of-two time-steps; the integrator around the force pass) ----------
+//
+// Aarseth's criterion (Aarseth 2003) with the higher derivatives of the
+// Hermite interpolation over the last step [t0, t1] (Makino & Aarseth 1992):
+//   a2(t0) = (-6 (a0 - a1) - dt (4 j0 + 2 j1)) / dt^2
+//   a3     = (12 (a0 - a1) + 6 dt (j0 + j1)) / dt^3
+//   a2(t1) = a2(t0) + dt a3
+//   dt'    = sqrt(eta (|a1| |a2(t1)| + |j1|^2) / (|j1| |a3| + |a2(t1)|^2))
+// quantised to the largest power of two not above dt', at most twice the last
+// step and dt_max, and dividing t1 (so the blocks stay synchronised).
+__device__ __forceinline__ double norm3(const double *p) { return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]); }
+
+__device__ __forceinline__ double quantise_dt(double want, double cap, double t1) {
+    double d = cap;
+    while (d > want && d > kBlockDtMin) d *= 0.5;
+    while (d > kBlockDtMin && fmod(t1, d) != 0.0) d *= 0.5;
+    return d;
+}
+
+// initial steps at t0 from |a| / |j| (the usual start of a Hermite run)
+__global__ void block_init_kernel(JStore js, double *dt, int64_t n, double eta_s, double dt_max, double t0) {
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double an = norm3(js.a + 3 * s), jn = norm3(js.jk + 3 * s);
+    const double want = (jn > 0.0) ? eta_s * an / jn : dt_max;
+    dt[s] = quantise_dt(want, dt_max, t0);
+    js.t[s] = t0;
+}
+
+// min over particles of t_i + dt_i, as the bits of a non-negative double
+__global__ void block_next_kernel(const double *t, const double *dt, int64_t n, unsigned long long *out) {
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    unsigned long long v = ~0ull;
+    if (s < n) v = static_cast<unsigned long long>(__double_as_longlong(t[s] + dt[s]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(out, v);
+}
+
+// slots whose next time is t1 (the active block), appended in any order
+__global__ void block_active_kernel(const double *t, const double *dt, int64_t n, const unsigned long long *t1bits,
+                                    int32_t *active, unsigned int *count) {
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    if (t[s] + dt[s] == __longlong_as_double(static_cast<long long>(*t1bits)))
+        active[atomicAdd(count, 1u)] = static_cast<int32_t>(s);
+}
+
+// Hermite-4 corrector and the next step for the active particles (a1, j1 at
+// the predicted state, position k of the active list); the double-single
+// cache follows the store.
+__global__ void block_correct_kernel(JStore js, double *dt, const int32_t *active, int64_t n_act, double t1,
+                                     const double *a1, const double *j1, double eta, double dt_max) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n_act) return;
+    const int64_t s = active[k];
+    const double h = t1 - js.t[s];
+    const double h2 = h * h;
+    double a2[3], a3[3], an[3], jn[3];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = 3 * s + c;
+        const double x0 = js.x[q], v0 = js.v[q], a0 = js.a[q], j0 = js.jk[q];
+        const double aa = a1[3 * k + c], jj = j1[3 * k + c];
+        const double v1 = v0 + (a0 + aa) * (h / 2) + (j0 - jj) * (h2 / 12);
+        const double x1 = x0 + (v0 + v1) * (h / 2) + (a0 - aa) * (h2 / 12);
+        const double a2_0 = (-6.0 * (a0 - aa) - h * (4.0 * j0 + 2.0 * jj)) / h2;
+        a3[c] = (12.0 * (a0 - aa) + 6.0 * h * (j0 + jj)) / (h2 * h);
+        a2[c] = a2_0 + h * a3[c];
+        an[c] = aa;
+        jn[c] = jj;
+        js.x[q] = x1;
+        js.v[q] = v1;
+        js.a[q] = aa;
+        js.jk[q] = jj;
+    }
+    js.t[s] = t1;
+    const double A = norm3(an), J = norm3(jn), A2 = norm3(a2), A3 = norm3(a3);
+    const double den = J * A3 + A2 * A2;
+    const double want = (den > 0.0) ? sqrt(eta * (A * A2 + J * J) / den) : dt_max;
+    dt[s] = quantise_dt(want, fmin(2.0 * h, dt_max), t1);
+    if (js.dsc) write_dscache(js, s);
 }
 
 __global__ void iota_kernel(int32_t *dst, int64_t n) {
@@ -358,6 +443,30 @@ cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const doubl
 cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     iota_kernel<<<grid_for(n), kThreads, 0, s>>>(dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_init(const JStore &js, double *dt, int64_t n, double eta_s, double dt_max, double t0,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    block_init_kernel<<<grid_for(n), kThreads, 0, s>>>(js, dt, n, eta_s, dt_max, t0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_select(const double *t, const double *dt, int64_t n, unsigned long long *t1bits,
+                                int32_t *active, unsigned int *count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(t1bits, 0xff, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    block_next_kernel<<<grid_for(n), kThreads, 0, s>>>(t, dt, n, t1bits);
+    block_active_kernel<<<grid_for(n), kThreads, 0, s>>>(t, dt, n, t1bits, active, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_correct(const JStore &js, double *dt, const int32_t *active, int64_t n_act, double t1,
+                                 const double *a1, const double *j1, double eta, double dt_max, cudaStream_t s) {
+    if (n_act <= 0) return cudaSuccess;
+    block_correct_kernel<<<grid_for(n_act), kThreads, 0, s>>>(js, dt, active, n_act, t1, a1, j1, eta, dt_max);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,9 @@ _SIGS = [
     ("sp2_compute", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_compute_range", [_P, c_int64, c_int64, c_int64, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_compute_nb", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P, c_int32, _P, _P, c_int], c_int),
+    ("sp2_get_j", [_P, c_int64, c_int64, _P, _P, _P, _P, _P, c_int], c_int),
+    ("sp2_block_init", [_P, c_double, c_double, c_double], c_int),
+    ("sp2_block_run", [_P, c_double, c_double, c_double, _P], c_int),
     ("sp2_batch_plan_create", [_P, c_int64, _P, POINTER(_P)], c_int),
     ("sp2_batch_plan_destroy", [_P], c_int),
     ("sp2_compute_batched", [_P, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
@@ -201,6 +204,27 @@ def sp2_compute_nb(ctx, i_idx, h2, nb_max, nb_count, nb_ids, acc=None, jerk=None
     pi, pa, pj, ps, pp, pid, pr2, ph2, pcnt, pids = ptrs
     _check(load().sp2_compute_nb(ctx, len(i_idx), pi, pa, pj, ps, pp, pid, pr2, ph2, int(nb_max), pcnt, pids, kind),
            ctx)
+
+
+class sp2_block_stats(Structure):
+    _fields_ = [("block_steps", c_int64), ("active_sum", c_int64), ("max_active", c_int64), ("min_active", c_int64),
+                ("t", c_double)]
+
+
+def sp2_get_j(ctx, first, n, x=None, v=None, a=None, jerk=None, t=None):
+    ptrs, kind, _k = _marshal([x, v, a, jerk, t], [F8, F8, F8, F8, F8])
+    _check(load().sp2_get_j(ctx, int(first), int(n), *ptrs, kind), ctx)
+
+
+def sp2_block_init(ctx, t0, eta_s, dt_max):
+    _check(load().sp2_block_init(ctx, float(t0), float(eta_s), float(dt_max)), ctx)
+
+
+def sp2_block_run(ctx, t_end, eta, dt_max):
+    """Advance with block time-steps to t_end; returns the statistics as a dict."""
+    st = sp2_block_stats()
+    _check(load().sp2_block_run(ctx, float(t_end), float(eta), float(dt_max), byref(st)), ctx)
+    return {name: getattr(st, name) for name, _ in st._fields_}
 
 
 def sp2_batch_plan_create(ctx, offsets):
@@ -350,6 +374,9 @@ class Context:
     def predict(self, t): return sp2_predict(self.ctx, t)
     def compute(self, *a, **k): return sp2_compute(self.ctx, *a, **k)
     def compute_nb(self, *a, **k): return sp2_compute_nb(self.ctx, *a, **k)
+    def get_j(self, *a, **k): return sp2_get_j(self.ctx, *a, **k)
+    def block_init(self, *a): return sp2_block_init(self.ctx, *a)
+    def block_run(self, *a): return sp2_block_run(self.ctx, *a)
     def batch_plan(self, offsets): return sp2_batch_plan_create(self.ctx, offsets)
     def compute_batched(self, *a, **k): return sp2_compute_batched(self.ctx, *a, **k)
     def forces(self, *a, **k): return sp2_forces(self.ctx, *a, **k)

@@ -1,0 +1,86 @@
+"""GPU block time-step Hermite-4 (sp2_block_init / sp2_block_run) against the
+oracle's block integrator: same number of blocks and active particles, final
+states within the differences that summation order (FP64) or the mixed
+precision force can cause, energy conserved; plus the state read-back and the
+argument rules."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp2():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_04068_gb300 import build, sp2 as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def _gpu_run(sp2, precision, m, x, v, eps2, t_end, eta, eta_s, dt_max):
+    n = len(m)
+    c = sp2.Context(order=4, precision=precision, n_max=n, eps2=eps2, with_nn=0)
+    z = np.zeros((n, 3))
+    c.set_j(0, np.arange(n, dtype=np.int32), m, x, v, z, z, None, np.zeros(n))
+    c.block_init(0.0, eta_s, dt_max)
+    st = c.block_run(t_end, eta, dt_max)
+    xs, vs, ts = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    c.get_j(0, n, x=xs, v=vs, t=ts)
+    c.close()
+    return xs, vs, ts, st
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_block_run_matches_oracle(sp2, oracle_mod, mixed):
+    n, eps2, t_end, eta, dt_max = 256, 1e-3, 2.0 ** -4, 0.02, 2.0 ** -6
+    m, x, v = W.plummer(n, 12)
+    xo, vo, to, so = oracle_mod.hermite4_block(m, x, v, eps2, t_end, eta, 0.01, dt_max)
+    xg, vg, tg, sg = _gpu_run(sp2, sp2.SP2_MIXED if mixed else sp2.SP2_FP64, m, x, v, eps2, t_end, eta, 0.01, dt_max)
+    assert np.all(tg == t_end) and np.all(to == t_end)
+    # time-step choices depend on the last bits; allow a few particles to step differently
+    assert abs(sg["block_steps"] - so["block_steps"]) <= 0.05 * so["block_steps"] + 1
+    assert abs(sg["active_sum"] - so["active_sum"]) <= 0.05 * so["active_sum"]
+    dx = np.linalg.norm(xg - xo, axis=1) / np.linalg.norm(xo, axis=1)
+    assert np.median(dx) < (1e-6 if mixed else 1e-12)
+    assert dx.max() < (1e-4 if mixed else 1e-8)
+    e0 = oracle_mod.energy(m, x, v, eps2)
+    eg = abs(oracle_mod.energy(m, xg, vg, eps2) / e0 - 1)
+    eo = abs(oracle_mod.energy(m, xo, vo, eps2) / e0 - 1)
+    assert eo < 1e-8
+    assert eg < (1e-6 if mixed else 1e-8)
+
+
+def test_block_run_in_stages_and_rules(sp2, oracle_mod):
+    n, eps2 = 200, 1e-3
+    m, x, v = W.plummer(n, 3)
+    c = sp2.Context(order=4, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0)
+    z = np.zeros((n, 3))
+    ids = np.arange(n, dtype=np.int32)
+    with pytest.raises(sp2.SP2Error):
+        c.block_run(0.1, 0.01, 2.0 ** -6)  # nothing loaded / not initialised
+    c.set_j(0, ids, m, x, v, z, z, None, np.zeros(n))
+    with pytest.raises(sp2.SP2Error):
+        c.block_run(0.1, 0.01, 2.0 ** -6)  # block_init missing
+    c.block_init(0.0, 0.01, 2.0 ** -6)
+    s1 = c.block_run(2.0 ** -5, 0.02, 2.0 ** -6)
+    s2 = c.block_run(2.0 ** -4, 0.02, 2.0 ** -6)  # continues where the first stopped
+    assert s1["t"] == 2.0 ** -5 and s2["t"] == 2.0 ** -4
+    xs, ts = np.empty((n, 3)), np.empty(n)
+    c.get_j(0, n, x=xs, t=ts)
+    assert np.all(ts == 2.0 ** -4)
+    xo, _, _, so = oracle_mod.hermite4_block(m, x, v, eps2, 2.0 ** -4, 0.02, 0.01, 2.0 ** -6)
+    assert abs(s1["block_steps"] + s2["block_steps"] - so["block_steps"]) <= 0.05 * so["block_steps"] + 1
+    assert np.max(np.abs(xs - xo)) < 1e-8
+    with pytest.raises(sp2.SP2Error):
+        c.get_j(0, n + 1, x=np.empty((n + 1, 3)))
+    c.close()
+    c = sp2.Context(order=6, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0)
+    c.set_j(0, ids, m, x, v, z, z, z, np.zeros(n))
+    with pytest.raises(sp2.SP2Error):  # order 4 only
+        c.block_init(0.0, 0.01, 2.0 ** -6)
+    c.close()
