@@ -259,7 +259,7 @@ struct PassOut {
 // Dynamic shared memory of a pass launch (the kernel side computes the same):
 // the kStages-deep record ring (none when the prediction is fused: the pass
 // predicts each tile from global memory), for the mixed force passes one tile of
-// pair records, and for the mixed policies the FP64 totals of every
+// pair records, and for the mixed policies the 8-byte running totals of every
 // (thread, sink, field).
 size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
     const size_t ring = fused ? 0 : static_cast<size_t>(kStagesDevice) * tile * rb;

@@ -100,11 +100,13 @@ __device__ __forceinline__ void nn_merge(double &d, int &id, double od, int oid)
 // Mixed precision force policy: positions as double-single (hi + lo FP32),
 // x_j - x_i formed as (hi_j - hi_i) + (lo_j - lo_i); rsqrt (SFU) and all terms
 // in FP32.  Sums are kept in two FP32 levels -- a partial over kChunk sources,
-// folded into a second FP32 level -- and the second level is added into FP64
-// totals (held in shared memory, one slot per thread and sink) every kFlush
-// sources.  Sequential FP32 summation rounds every add at the scale of the
-// running sum, so a long FP32 sum dominated by one large term loses ~sqrt(k)
-// ulps; the two short levels bound that error by ~(kChunk + kFlush/kChunk) ulps.
+// folded into a second FP32 level -- and the second level is added into
+// running totals once at least kFlush sources have passed (at a tile end in
+// the pass kernel): FP64 totals here (the batched kernel keeps them in
+// registers), double-single totals in shared memory in the paired policy.
+// Sequential FP32 summation rounds every add at the scale of the running sum,
+// so a long FP32 sum dominated by one large term loses ~sqrt(k) ulps; the two
+// short levels bound that error by ~(kChunk + sources per flush / kChunk) ulps.
 // ---------------------------------------------------------------------------
 template <int ORDER, bool NN>
 struct MixedForce {
@@ -1225,7 +1227,8 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
 }
 
 // Shared memory: kStages tiles of records, (paired policies) one tile of pair
-// records, then (mixed policies) the FP64 totals, [sink k][field f][thread]
+// records, then (mixed policies) the running totals (8 bytes each: FP64, or a
+// double-single pair in the paired policy), [sink k][field f][thread]
 // so each thread owns its slots.
 template <class P, int IPT, bool FUSED>
 __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
