@@ -56,11 +56,13 @@ def parse():
     p.add_argument("--n", type=int, default=131072)
     p.add_argument("--n-active", type=int, default=131072)
     p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint / lists lines")
-    p.add_argument("--extras", default="sweep,h6,batched,adjoint,nb,h2,blk",
+    p.add_argument("--extras", default="c1,sweep,h6,batched,adjoint,nb,h2,blk",
                    help="comma-separated secondary sections to run: sweep, h6, batched, adjoint")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                   help="precision of the headline step (profiling the FP64 kernel; the metric is quoted on mixed)")
     p.add_argument("--launch", default=None,
                    help="force the force-kernel launch shape: threads,i_per_thread,j_lanes,j_tile,split_j")
     return p.parse_args()
@@ -277,8 +279,8 @@ def run_ours(args, world, rank, local):
                nn_r2=torch.empty(n_act, dtype=torch.float64, device=dev))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
-        ctx = sp2.Context(order=4, precision=sp2.SP2_MIXED, n_max=n, eps2=eps2, profile=1,
-                          cuda_stream=stream.cuda_stream)
+        prec = sp2.SP2_MIXED if args.precision == "mixed" else sp2.SP2_FP64
+        ctx = sp2.Context(order=4, precision=prec, n_max=n, eps2=eps2, profile=1, cuda_stream=stream.cuda_stream)
         ctx.set_j(0, full["ids"], full["m"], full["x"], full["v"], full["a"], full["jerk"], None, full["tj"])
         ctx.predict(w["t"])
         if args.launch:
@@ -336,8 +338,11 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "n_active": n_act, "order": 4, "precision": "mixed",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.precision == "mixed" else WORKLOAD.replace(
+                       "mixed precision (double-single positions, FP32 terms, FP64 reduction)", "FP64"),
+                   "n": n, "n_active": n_act, "order": 4, "precision": args.precision,
                    "eps": 1e-4, "nearest_neighbour": True, "parallelism": f"replicas{world}",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, outside the step events)",
                    "launch": launch, "autotuned": tuned is not None,
@@ -353,6 +358,8 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if args.precision != "mixed":
+        line["roofline"] = None  # the FP32 FMA-pipe roofline describes the mixed kernel only
     if world == 1 and rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, n)
     if not args.no_e2e:
@@ -412,6 +419,8 @@ def extras(sp2, w, n, eps2, dev, stream, sections):
     D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
     res = {}
     with torch.cuda.stream(stream):
+        if "c1" in sections:
+            res["c1"] = bench_c1(sp2, dev, stream)
         if "sweep" in sections:
             res["sweep"] = sweep(sp2, w, n, eps2, dev, stream)
         if "h6" in sections:
@@ -427,6 +436,38 @@ def extras(sp2, w, n, eps2, dev, stream, sections):
         if "blk" in sections:
             res["blk"] = bench_blk(sp2, dev, stream)
     return res
+
+
+def bench_c1(sp2, dev, stream):
+    """Plain FP64 Hermite-4 pass, N = 1024 equal-mass Plummer, eps = 1e-3, all
+    particles active: one predict + compute (acc, jerk, pot, nearest
+    neighbour) per step, and the same through a CUDA graph."""
+    import torch
+    n = 1024
+    m, x, v = W.plummer(n, 0)
+    a, jk, _ = W.derivative_noise(n, 1, scales=(1.0, 4.0, 16.0))
+    ids = W.particle_ids(n)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
+    c = sp2.Context(order=4, precision=sp2.SP2_FP64, n_max=n, eps2=1e-6, cuda_stream=stream.cuda_stream)
+    c.set_j(0, D(ids), D(m), D(x), D(v), D(a), D(jk), None, D(np.zeros(n)))
+    idx = D(np.arange(n, dtype=np.int32))
+    o = dict(acc=torch.empty((n, 3), dtype=torch.float64, device=dev),
+             jerk=torch.empty((n, 3), dtype=torch.float64, device=dev),
+             pot=torch.empty(n, dtype=torch.float64, device=dev),
+             nn_id=torch.empty(n, dtype=torch.int32, device=dev),
+             nn_r2=torch.empty(n, dtype=torch.float64, device=dev))
+    c.predict(0.0)
+    c.autotune(n)
+    fn = lambda: (c.predict(0.0), c.compute(idx, **o))  # noqa: E731
+    ms = timed(fn, 50, stream)
+    sp2.sp2_graph_begin(c.ctx)
+    fn()
+    g = sp2.sp2_graph_end(c.ctx)
+    gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), 50, stream)
+    sp2.sp2_graph_destroy(g)
+    c.close()
+    return {"n": n, "us_per_step": 1e3 * ms, "graph_us_per_step": 1e3 * gms,
+            "interactions_per_s": n * n / (ms / 1e3)}
 
 
 def sweep(sp2, w, n, eps2, dev, stream):
@@ -467,6 +508,10 @@ def sweep(sp2, w, n, eps2, dev, stream):
                 gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), reps, stream)
                 sp2.sp2_graph_destroy(g)
                 row["mixed_graph_us_per_step"] = 1e3 * gms
+                if na <= 64:
+                    # the fused pass reads each source's double-single cache
+                    # once (112 B); the sweep does not flush L2 between steps
+                    row["mixed_jstream_gbs_l2_warm"] = n * 112 / (ms / 1e3) / 1e9
                 if na <= 1024:
                     # the paper's 1D form: one thread per sink, no source split
                     tuned_shape = c.get_launch(na)

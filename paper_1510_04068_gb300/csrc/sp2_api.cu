@@ -1066,7 +1066,9 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
     acc.min_active = INT64_MAX;
     acc.t = -1.0;
     for (;;) {
+        ev_begin(c, ST_OTHER);
         SP2_CK(c, launch_block_select(c->js.t, c->blk_dt, n, t1bits, c->blk_active, count, c->stream));
+        ev_end(c, ST_OTHER);
         unsigned int hw[4];
         SP2_CK(c, cudaMemcpyAsync(hw, c->dev_words + 6, sizeof hw, cudaMemcpyDeviceToHost, c->stream));
         SP2_CK(c, cudaStreamSynchronize(c->stream));
@@ -1082,7 +1084,9 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
         o.jerk = j1;
         SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec, c->rb, n, c->blk_active, n_act, 0, n, o, nullptr, ST_FORCE,
                          nullptr, true));
+        ev_begin(c, ST_OTHER);
         SP2_CK(c, launch_block_correct(c->js, c->blk_dt, c->blk_active, n_act, t1, a1, j1, eta, dt_max, c->stream));
+        ev_end(c, ST_OTHER);
         c->launches += 1;
         c->rec_valid = false;
         acc.block_steps += 1;
