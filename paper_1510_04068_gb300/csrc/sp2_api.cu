@@ -1216,7 +1216,10 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     auto split_for = [&](const sp2_launch &L, int rounds, int occ) -> int {
         const int64_t n_iblk = ceil_div(n_i, int64_t(L.threads / L.j_lanes) * L.i_per_thread);
         const int64_t slots = int64_t(c->sm_count) * occ;
-        const int64_t max_split = std::min<int64_t>(max_split_all, std::max<int64_t>(1, n_j / (2 * L.j_tile)));
+        // slices of at least two tiles keep the cp.async ring busy; the fused
+        // pass (one i-block, mixed) has no ring, so one tile per slice is fine
+        const int64_t min_tiles = (mixed && c->js.dsc && n_iblk == 1) ? 1 : 2;
+        const int64_t max_split = std::min<int64_t>(max_split_all, std::max<int64_t>(1, n_j / (min_tiles * L.j_tile)));
         int64_t split = ceil_div(rounds * slots, n_iblk);
         for (int64_t s2 = split; s2 <= split + 2 && s2 <= max_split; ++s2)
             if ((n_iblk * s2) % slots == 0) { split = s2; break; }
