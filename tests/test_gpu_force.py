@@ -186,3 +186,18 @@ def test_fused_prediction_small_n_active(sp2, oracle_mod, order):
         r = oracle_ref(oracle_mod, s, idx, order=order, eps2=eps2)
         e = np.linalg.norm(acc.cpu().numpy() - r["acc"], axis=1) / r["sc_acc"]
         assert e.max() <= 1e-6
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("n_i,split", [(1, 300), (3, 100), (5, 64), (2, 33)])
+def test_in_pass_reduction_levels(sp2, oracle_mod, mixed, n_i, split):
+    """Few sinks over many slices: the last CTA of each i-block reduces the
+    slices in FP64 (a warp per field), one to a few hundred of them; the result
+    matches the oracle."""
+    n, eps2 = 20000, 1e-8
+    s = state(n, 90 + n_i, order=4)
+    idx = np.sort(np.random.default_rng(split).choice(n, n_i, replace=False)).astype(np.int32)
+    launch = dict(threads=64, i_per_thread=1, j_lanes=8, j_tile=64, split_j=split, ctas_per_sm=0)
+    g = gpu_run(sp2, s, idx, order=4, precision=sp2.SP2_MIXED if mixed else sp2.SP2_FP64, eps2=eps2, launch=launch)
+    r = oracle_ref(oracle_mod, s, idx, order=4, eps2=eps2)
+    check(g, r, order=4, mixed=mixed, s=s, i_idx=idx, label=f"split={split}")

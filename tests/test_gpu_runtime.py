@@ -177,3 +177,41 @@ def test_profile_and_launch_counts(env):
     assert p["predict"][0] == 3 and p["force"][0] == 3
     assert p["force"][1] > 0 and p["predict"][1] > 0
     c.close()
+
+
+def test_repeated_calls_are_bit_identical():
+    """The reductions have a fixed order, so the same call gives the same bits
+    every time, whichever CTA finishes last; shapes with the in-pass reduction
+    over few and many slices and with the separate reduction kernel."""
+    import torch
+    from paper_1510_04068_gb300 import build, sp2
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    sp2.load()
+    import workloads as W
+    n = 30000
+    m, x, v = W.plummer(n, 3)
+    a, jk, _ = W.derivative_noise(n, 4, scales=(1.0, 4.0, 16.0))
+    ids = W.particle_ids(n, 5)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).cuda()  # noqa: E731
+    for prec in (sp2.SP2_MIXED, sp2.SP2_FP64):
+        c = sp2.Context(order=4, precision=prec, n_max=n, eps2=1e-8)
+        c.set_j(0, D(ids), D(m), D(x), D(v), D(a), D(jk), None, D(W.block_times(n, 6, 1.0)))
+        for n_i, shape in ((1, (64, 1, 32, 256, 100)), (3, (64, 1, 8, 64, 400)), (4000, (128, 1, 1, 128, 60))):
+            idx = D(np.sort(np.random.default_rng(n_i).choice(n, n_i, replace=False)).astype(np.int32))
+            c.set_launch(n_i, dict(zip(("threads", "i_per_thread", "j_lanes", "j_tile", "split_j"), shape), ctas_per_sm=0))
+            outs = []
+            for _ in range(3):
+                c.predict(1.0)
+                o = dict(acc=torch.empty((n_i, 3), dtype=torch.float64, device="cuda"),
+                         jerk=torch.empty((n_i, 3), dtype=torch.float64, device="cuda"),
+                         pot=torch.empty(n_i, dtype=torch.float64, device="cuda"),
+                         nn_id=torch.empty(n_i, dtype=torch.int32, device="cuda"),
+                         nn_r2=torch.empty(n_i, dtype=torch.float64, device="cuda"))
+                c.compute(idx, **o)
+                outs.append({k: t.cpu().numpy() for k, t in o.items()})
+            for o2 in outs[1:]:
+                for k in o2:
+                    assert np.array_equal(outs[0][k].view(np.uint8), o2[k].view(np.uint8)), (prec, n_i, k)
+        c.close()
