@@ -277,9 +277,10 @@ sp2_status sp2_hermite4_step_vjp(sp2_ctx *ctx, int64_t n, double dt, const doubl
 
 /* Launch-shape control.  sp2_autotune times candidate launch shapes for sink
  * counts n_i on the current predicted records (Sec. 3.1: the block / thread
- * configuration is tuned per GPU) and caches the best for that size bucket;
- * sp2_get_launch reports what sp2_compute would use for n_i; sp2_set_launch
- * overrides it for n_i's bucket (validated: SP2_ERR_ARG). */
+ * configuration is tuned per GPU) and caches the best for the power-of-two
+ * buckets of n_i and of the loaded source count; sp2_get_launch reports what
+ * sp2_compute would use for n_i; sp2_set_launch overrides it for those
+ * buckets (validated: SP2_ERR_ARG). */
 sp2_status sp2_autotune(sp2_ctx *ctx, int64_t n_i, sp2_launch *best);
 sp2_status sp2_get_launch(sp2_ctx *ctx, int64_t n_i, sp2_launch *out);
 sp2_status sp2_set_launch(sp2_ctx *ctx, int64_t n_i, const sp2_launch *in);

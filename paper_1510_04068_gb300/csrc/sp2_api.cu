@@ -77,7 +77,7 @@ struct sp2_ctx {
     size_t stage_cap = 0;
     std::vector<void *> owned;       // everything allocated (for close)
 
-    std::map<int64_t, sp2_launch> tuned;  // key: bucket of n_i
+    std::map<int64_t, sp2_launch> tuned;  // key: tune_key(n_i, n_j)
     // profiling: per stage a ring of (start, stop) event pairs
     std::vector<cudaEvent_t> ev[ST_COUNT];
     int64_t ev_count[ST_COUNT] = {};
@@ -198,6 +198,8 @@ int64_t bucket_of(int64_t n_i) {
     return b;
 }
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+// autotuner cache key: the power-of-two buckets of the sink and source counts
+int64_t tune_key(int64_t n_i, int64_t n_j) { return bucket_of(n_i) * 64 + bucket_of(std::max<int64_t>(n_j, 1)); }
 
 sp2_status check_launch(sp2_ctx *c, const sp2_launch &L) {
     if (!(L.threads == 32 || L.threads == 64 || L.threads == 128 || L.threads == 256))
@@ -282,7 +284,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     if (forced) {
         L = *forced;
     } else {
-        auto it = (kind == K_FORCE) ? c->tuned.find(bucket_of(n_i)) : c->tuned.end();
+        auto it = (kind == K_FORCE) ? c->tuned.find(tune_key(n_i, j_end - j_begin)) : c->tuned.end();
         L = (it != c->tuned.end()) ? it->second : heuristic(c, kind, mixed, n_i, j_end - j_begin);
     }
     const int nb = (kind == K_FORCE && nn && o.nb_count) ? 1 : 0;
@@ -1147,7 +1149,7 @@ sp2_status sp2_hermite4_step_vjp(sp2_ctx *c, int64_t n, double dt, const double 
 sp2_status sp2_get_launch(sp2_ctx *c, int64_t n_i, sp2_launch *out) {
     SP2_CKS(usable(c));
     if (!out || n_i <= 0) return fail(c, SP2_ERR_ARG, "bad arguments");
-    auto it = c->tuned.find(bucket_of(n_i));
+    auto it = c->tuned.find(tune_key(n_i, c->n_loaded));
     *out = (it != c->tuned.end()) ? it->second
                                   : heuristic(c, K_FORCE, c->cfg.precision == SP2_MIXED, n_i, std::max<int64_t>(c->n_loaded, 1));
     return SP2_OK;
@@ -1157,7 +1159,7 @@ sp2_status sp2_set_launch(sp2_ctx *c, int64_t n_i, const sp2_launch *in) {
     SP2_CKS(usable(c));
     if (!in || n_i <= 0) return fail(c, SP2_ERR_ARG, "bad arguments");
     SP2_CKS(check_launch(c, *in));
-    c->tuned[bucket_of(n_i)] = *in;
+    c->tuned[tune_key(n_i, c->n_loaded)] = *in;
     return SP2_OK;
 }
 
@@ -1278,7 +1280,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         if (st != SP2_OK) return st;
         if (ms < best_ms) { best_ms = ms; best_k = k; }
     }
-    c->tuned[bucket_of(n_i)] = cand[best_k];
+    c->tuned[tune_key(n_i, n_j)] = cand[best_k];
     if (best) *best = cand[best_k];
     return SP2_OK;
 }

@@ -215,3 +215,40 @@ def test_repeated_calls_are_bit_identical():
                 for k in o2:
                     assert np.array_equal(outs[0][k].view(np.uint8), o2[k].view(np.uint8)), (prec, n_i, k)
         c.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_outputs_not_written_past_their_end(precision):
+    """Canary-padded outputs: for ragged sink counts and several launch shapes
+    (one and many i-blocks, split and not, fused and separate reduction) the
+    library writes exactly n_i entries of every output."""
+    import torch
+    from paper_1510_04068_gb300 import build, sp2
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    sp2.load()
+    s = state(5000, 11)
+    D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).cuda()  # noqa: E731
+    prec = sp2.SP2_MIXED if precision == "mixed" else sp2.SP2_FP64
+    c = sp2.Context(order=4, precision=prec, n_max=5000, eps2=1e-8)
+    c.set_j(0, D(s["ids"]), D(s["m"]), D(s["x"]), D(s["v"]), D(s["a"]), D(s["jerk"]), None, D(s["tj"]))
+    pad = 64
+    for n_i, shape in ((1, (32, 1, 32, 256, 16)), (37, (64, 2, 2, 64, 30)), (777, (128, 4, 1, 128, 3)),
+                       (1001, (256, 1, 1, 512, 1)), (5000, (128, 2, 1, 256, 40))):
+        idx = D(np.sort(np.random.default_rng(n_i).choice(5000, n_i, replace=False)).astype(np.int32))
+        c.predict(1.0)
+        c.set_launch(n_i, dict(zip(("threads", "i_per_thread", "j_lanes", "j_tile", "split_j"), shape), ctas_per_sm=0))
+        bufs = dict(acc=torch.full(((n_i + pad) * 3,), 7.25, dtype=torch.float64, device="cuda"),
+                    jerk=torch.full(((n_i + pad) * 3,), 7.25, dtype=torch.float64, device="cuda"),
+                    pot=torch.full((n_i + pad,), 7.25, dtype=torch.float64, device="cuda"),
+                    nn_id=torch.full((n_i + pad,), -77, dtype=torch.int32, device="cuda"),
+                    nn_r2=torch.full((n_i + pad,), 7.25, dtype=torch.float64, device="cuda"))
+        c.compute(idx, **bufs)
+        c.sync()
+        for k, b in bufs.items():
+            w = 3 if k in ("acc", "jerk") else 1
+            tail = b[n_i * w:].cpu().numpy()
+            assert np.all(tail == (-77 if k == "nn_id" else 7.25)), (n_i, shape, k)
+            assert np.all(np.isfinite(b[:n_i * w].cpu().numpy().astype(np.float64))), (n_i, k)
+    c.close()
