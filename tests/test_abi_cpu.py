@@ -97,3 +97,45 @@ def test_binding_refuses_mixed_host_and_device(lib):
     from paper_1510_04068_gb300 import sp2
     with pytest.raises(TypeError):
         sp2._marshal([np.zeros(3), np.zeros(3, np.float32)], [np.float64, np.float64])
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "sapporo_gb.h"
+
+/* A plain C99 caller of the ABI: config defaults and argument validation,
+   which need no GPU. */
+int main(void) {
+    sp2_config cfg;
+    sp2_ctx *ctx = NULL;
+    sp2_config_default(&cfg);
+    cfg.n_max = 16;
+    cfg.order = 3;
+    if (sp2_open(&ctx, &cfg) != SP2_ERR_ARG || ctx != NULL) return 1;
+    if (sp2_close(NULL) != SP2_OK) return 2;
+    printf("%s\n", sp2_strerror(SP2_ERR_RANGE));
+    return 0;
+}
+"""
+
+
+def test_header_compiles_and_links_as_c(lib, tmp_path):
+    """include/sapporo_gb.h is a C header: a C99 client compiles with warnings
+    as errors, links against the library and runs the GPU-free calls."""
+    import shutil
+    import subprocess
+    from paper_1510_04068_gb300 import build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = str(build.LIB.parent)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", f"-I{ROOT / 'include'}",
+                        str(src), "-o", str(exe), f"-L{libdir}", "-lsapporo_gb", f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.strip()
