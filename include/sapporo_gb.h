@@ -161,6 +161,20 @@ sp2_status sp2_compute_range(sp2_ctx *ctx, int64_t j_begin, int64_t j_end,
                              double *acc, double *jerk, double *snap, double *pot,
                              int32_t *nn_id, double *nn_r2, int ptr_kind);
 
+/* Forces on explicit sinks (the GRAPE-style form of the call, in which the
+ * integrator sends the i-particles' own predicted state; Sec. 2.2.4 names the
+ * i-particle data sent to the device): sink k has position xi[k], velocity
+ * vi[k] and, for order 6, acceleration ai[k] (each [n_i x 3] double; vi may be
+ * NULL for order 2).  i_slot[k] names the loaded slot that is the sink itself
+ * (its self pair is skipped), or is negative when the sink is not one of the
+ * loaded particles; i_slot == NULL means no sink is.  The sources are the
+ * predicted records as for sp2_compute; outputs and errors as sp2_compute.
+ * The paper has no separate call for this (the GRAPE API it implements does). */
+sp2_status sp2_compute_ext(sp2_ctx *ctx, int64_t n_i, const int32_t *i_slot,
+                           const double *xi, const double *vi, const double *ai,
+                           double *acc, double *jerk, double *snap, double *pot,
+                           int32_t *nn_id, double *nn_r2, int ptr_kind);
+
 /* sp2_compute plus neighbour lists (Sec. 1: the library can return, for each
  * particle, the list of all particles within a given radius; Sec. 3: the
  * perturber lists of NBODY4-style integrators).  For sink k (position k of

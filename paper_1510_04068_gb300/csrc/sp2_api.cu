@@ -69,6 +69,9 @@ struct sp2_ctx {
     size_t part_cap = 0, part_id_cap = 0;   // bytes
     unsigned int *done = nullptr;           // per-i-block arrival counters of the fused reduction
     size_t done_cap = 0;                    // bytes
+    unsigned char *sinkrec = nullptr;       // records of explicit sinks
+    int32_t *noslot = nullptr;              // -1 per explicit sink (no self pair)
+    size_t sinkrec_cap = 0, noslot_cap = 0;
     double *blk_dt = nullptr;               // block time-steps: per-slot step
     int32_t *blk_active = nullptr;          // block time-steps: active slots
     size_t blk_dt_cap = 0, blk_active_cap = 0;
@@ -252,6 +255,8 @@ struct PassOut {
     double *nn_r2 = nullptr;
     double *xbar = nullptr, *vbar = nullptr, *mbar = nullptr;
     int accumulate = 0;
+    // explicit sinks (optional): sink i is sink_rec[i]; i_idx then names slots for the self pair
+    const unsigned char *sink_rec = nullptr;
     // neighbour lists (optional): squared radii per sink, capacity, counts, lists
     const double *nb_h2 = nullptr;
     int nb_max = 0;
@@ -335,6 +340,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     p.eps2 = c->cfg.eps2;
     p.acc = o.acc; p.jerk = o.jerk; p.snap = o.snap; p.pot = o.pot; p.nn_id = o.nn_id; p.nn_r2 = o.nn_r2;
     p.xbar = o.xbar; p.vbar = o.vbar; p.mbar = o.mbar; p.accumulate = o.accumulate;
+    p.sink_rec = o.sink_rec;
     if (nb) {
         p.nb_h2 = o.nb_h2;
         p.nb_count = o.nb_count;
@@ -825,6 +831,67 @@ sp2_status sp2_compute(sp2_ctx *c, int64_t n_i, const int32_t *i_idx, double *ac
     SP2_CKS(usable(c));
     if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
     return sp2_compute_range(c, 0, c->n_loaded, n_i, i_idx, acc, jerk, snap, pot, nn_id, nn_r2, ptr_kind);
+}
+
+sp2_status sp2_compute_ext(sp2_ctx *c, int64_t n_i, const int32_t *i_slot, const double *xi, const double *vi,
+                           const double *ai, double *acc, double *jerk, double *snap, double *pot, int32_t *nn_id,
+                           double *nn_r2, int ptr_kind) {
+    SP2_CKS(usable(c));
+    SP2_CKS(check_ptr_kind(c, ptr_kind));
+    if (n_i < 0) return fail(c, SP2_ERR_ARG, "n_i < 0");
+    if (n_i == 0) return SP2_OK;
+    if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
+    if (!c->rec_valid) return fail(c, SP2_ERR_STATE, "predicted records are stale: call sp2_predict first");
+    if (n_i > (int64_t(1) << 30)) return fail(c, SP2_ERR_RANGE, "n_i too large");
+    const int order = c->cfg.order;
+    if (!xi || (order != 2 && !vi) || (order == 6 && !ai))
+        return fail(c, SP2_ERR_ARG, "explicit sinks need x, v (orders 4, 6) and a (order 6)");
+    if (snap && order != 6) return fail(c, SP2_ERR_ARG, "snap requested from a context below order 6");
+    if (jerk && order == 2) return fail(c, SP2_ERR_ARG, "jerk requested from an order-2 (leap-frog) context");
+    if ((nn_id || nn_r2) && !c->cfg.with_nn) return fail(c, SP2_ERR_UNSUPPORTED, "context opened without nearest neighbour");
+    const int mixed = c->cfg.precision == SP2_MIXED;
+    PassOut o;
+    Staging s{c};
+    const int32_t *d_slot = i_slot;
+    if (ptr_kind == SP2_HOST) {
+        if (i_slot)
+            for (int64_t k = 0; k < n_i; ++k)
+                if (i_slot[k] >= c->n_loaded) return fail(c, SP2_ERR_RANGE, "slot %d outside the loaded set", i_slot[k]);
+        const size_t v3 = 3 * n_i * sizeof(double), v1 = n_i * sizeof(double);
+        s.plan(n_i * 4); s.plan(v3); s.plan(v3); s.plan(v3);
+        s.plan(v3); s.plan(v3); s.plan(v3); s.plan(v1); s.plan(n_i * 4); s.plan(v1);
+        SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->stage), &c->stage_cap, s.total, "staging"));
+        d_slot = stage_in(s, i_slot, n_i);
+        xi = stage_in(s, xi, 3 * n_i);
+        vi = stage_in(s, vi, 3 * n_i);
+        ai = stage_in(s, ai, 3 * n_i);
+        o.acc = stage_out(s, acc, 3 * n_i);
+        o.jerk = stage_out(s, jerk, 3 * n_i);
+        o.snap = stage_out(s, snap, 3 * n_i);
+        o.pot = stage_out(s, pot, n_i);
+        o.nn_id = stage_out(s, nn_id, n_i);
+        o.nn_r2 = stage_out(s, nn_r2, n_i);
+        SP2_CKS(stage_copy_in(s));
+    } else {
+        o.acc = acc; o.jerk = jerk; o.snap = snap; o.pot = pot; o.nn_id = nn_id; o.nn_r2 = nn_r2;
+    }
+    if (!d_slot) {
+        SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->noslot), &c->noslot_cap, n_i * sizeof(int32_t), "sink-slot"));
+        SP2_CK(c, cudaMemsetAsync(c->noslot, 0xff, n_i * sizeof(int32_t), c->stream));
+        d_slot = c->noslot;
+    }
+    SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->sinkrec), &c->sinkrec_cap, n_i * c->rb, "sink-record"));
+    SP2_CK(c, launch_pack_sinks(order, mixed, n_i, xi, vi, ai, c->sinkrec, c->stream));
+    c->launches += 1;
+    o.sink_rec = c->sinkrec;
+    const int nn = c->cfg.with_nn && (o.nn_id || o.nn_r2);
+    SP2_CKS(run_pass(c, K_FORCE, order, mixed, nn, c->rec, c->rb, c->n_loaded, d_slot, n_i, 0, c->n_loaded, o,
+                     nullptr, ST_FORCE, nullptr, true));
+    const double *arrs[4] = {o.acc, o.jerk, o.snap, o.pot};
+    const int64_t lens[4] = {3 * n_i, 3 * n_i, 3 * n_i, n_i};
+    SP2_CKS(finite_check(c, arrs, lens, 4));
+    if (ptr_kind == SP2_HOST) SP2_CKS(stage_copy_out(s));
+    return SP2_OK;
 }
 
 sp2_status sp2_compute_nb(sp2_ctx *c, int64_t n_i, const int32_t *i_idx, double *acc, double *jerk, double *snap,

@@ -1289,14 +1289,24 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             ii[k] = iblk * p.sinks_per_cta + static_cast<int64_t>(k) * slots + islot;
             val[k] = ii[k] < p.n_i;
             const int raw = val[k] ? __ldg(p.i_idx + ii[k]) : 0;
-            if (val[k] && (raw < 0 || raw >= p.n_loaded)) {
-                atomicOr(p.err, 1u);  // reported by sp2_sync; this sink is skipped
-                val[k] = false;
+            if (p.sink_rec) {
+                // explicit sink: its own record; raw names its slot for the self pair (< 0: none)
+                if (val[k] && raw >= p.n_loaded) {
+                    atomicOr(p.err, 1u);
+                    val[k] = false;
+                }
+                P::load_sink(p.sink_rec, val[k] ? ii[k] : 0, sk[k]);
+                sk[k].slot = (val[k] && raw >= 0) ? raw : -1;
+            } else {
+                if (val[k] && (raw < 0 || raw >= p.n_loaded)) {
+                    atomicOr(p.err, 1u);  // reported by sp2_sync; this sink is skipped
+                    val[k] = false;
+                }
+                const int slot = val[k] ? raw : static_cast<int>(p.j_begin);
+                if constexpr (FUSED && P::kCanFuse) P::sink_from(P::predict(p.dsc, slot, p.t_hi, p.t_lo), sk[k]);
+                else P::load_sink(p.rec, slot, sk[k]);
+                sk[k].slot = val[k] ? slot : -1;
             }
-            const int slot = val[k] ? raw : static_cast<int>(p.j_begin);
-            if constexpr (FUSED && P::kCanFuse) P::sink_from(P::predict(p.dsc, slot, p.t_hi, p.t_lo), sk[k]);
-            else P::load_sink(p.rec, slot, sk[k]);
-            sk[k].slot = val[k] ? slot : -1;
             if constexpr (is_nb<P>::value) P::set_nb(sk[k], p, ii[k], val[k]);
             P::init(ac[k]);
             P::zero_totals(tot + k * P::NS * nt, nt);

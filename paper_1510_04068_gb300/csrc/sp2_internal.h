@@ -42,7 +42,8 @@ inline int vjp_record_bytes(int mixed) { return mixed ? 80 : 112; }
 // (i-block, j-slice); see sp2_device.cuh).
 struct ForceParams {
     const unsigned char *rec;  // predicted records, slot 0
-    const int32_t *i_idx;      // sink slots (n_i)
+    const int32_t *i_idx;      // sink slots (n_i); with sink_rec: slot for the self pair, or < 0 for none
+    const unsigned char *sink_rec;  // explicit sinks: record of sink position i (null: sinks are rec[i_idx[i]])
     int64_t n_i;
     int64_t j_begin, j_end;    // source slots [j_begin, j_end)
     int64_t slice_len;         // sources per slice
@@ -179,6 +180,9 @@ cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n
 // (m, x, v) -> order-4 records with no prediction (all-pairs entry points)
 cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const double *x,
                               const double *v, unsigned char *rec, cudaStream_t s);
+// explicit sinks in the context's record format (order 2 and 4 share one)
+cudaError_t launch_pack_sinks(int order, int mixed, int64_t n, const double *x, const double *v, const double *a,
+                              unsigned char *rec, cudaStream_t s);
 cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
 // Block time-steps (Hermite-4 with individual power-of-two steps).
 cudaError_t launch_block_init(const JStore &js, double *dt, int64_t n, double eta_s, double dt_max, double t0,

@@ -273,6 +273,23 @@ __global__ void block_correct_kernel(JStore js, double *dt, const int32_t *activ
     if (js.dsc) write_dscache(js, s);
 }
 
+// Explicit sinks (sp2_compute_ext): positions / velocities [/ accelerations]
+// given by the caller, packed in the context's record format.
+template <int ORDER, bool MIXED>
+__global__ void pack_sinks_kernel(int64_t n, const double *x, const double *v, const double *a, unsigned char *rec) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double xp[3], vp[3], ap[3];
+    for (int c = 0; c < 3; ++c) {
+        xp[c] = x[3 * j + c];
+        vp[c] = v ? v[3 * j + c] : 0.0;
+        ap[c] = (ORDER == 6) ? a[3 * j + c] : 0.0;
+    }
+    const int rb = MIXED ? (ORDER == 6 ? 64 : 48) : (ORDER == 6 ? 96 : 64);
+    if (MIXED) store_mixed(rec, rb, j, xp, vp, ORDER == 6 ? ap : nullptr, 0.0, -1);
+    else store_fp64(rec, rb, j, xp, vp, ORDER == 6 ? ap : nullptr, 0.0, -1);
+}
+
 __global__ void iota_kernel(int32_t *dst, int64_t n) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j < n) dst[j] = static_cast<int32_t>(j);
@@ -437,6 +454,20 @@ cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const doubl
     if (n <= 0) return cudaSuccess;
     if (mixed) pack_state_kernel<true><<<grid_for(n), kThreads, 0, s>>>(n, m, x, v, rec);
     else pack_state_kernel<false><<<grid_for(n), kThreads, 0, s>>>(n, m, x, v, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_sinks(int order, int mixed, int64_t n, const double *x, const double *v, const double *a,
+                              unsigned char *rec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned g = grid_for(n);
+    if (order == 6) {
+        if (mixed) pack_sinks_kernel<6, true><<<g, kThreads, 0, s>>>(n, x, v, a, rec);
+        else pack_sinks_kernel<6, false><<<g, kThreads, 0, s>>>(n, x, v, a, rec);
+    } else {
+        if (mixed) pack_sinks_kernel<4, true><<<g, kThreads, 0, s>>>(n, x, v, a, rec);
+        else pack_sinks_kernel<4, false><<<g, kThreads, 0, s>>>(n, x, v, a, rec);
+    }
     return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ _SIGS = [
     ("sp2_compute", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_compute_range", [_P, c_int64, c_int64, c_int64, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_compute_nb", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P, c_int32, _P, _P, c_int], c_int),
+    ("sp2_compute_ext", [_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_get_j", [_P, c_int64, c_int64, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_block_init", [_P, c_double, c_double, c_double], c_int),
     ("sp2_block_run", [_P, c_double, c_double, c_double, _P], c_int),
@@ -204,6 +205,15 @@ def sp2_compute_nb(ctx, i_idx, h2, nb_max, nb_count, nb_ids, acc=None, jerk=None
     pi, pa, pj, ps, pp, pid, pr2, ph2, pcnt, pids = ptrs
     _check(load().sp2_compute_nb(ctx, len(i_idx), pi, pa, pj, ps, pp, pid, pr2, ph2, int(nb_max), pcnt, pids, kind),
            ctx)
+
+
+def sp2_compute_ext(ctx, xi, vi=None, ai=None, i_slot=None, acc=None, jerk=None, snap=None, pot=None, nn_id=None,
+                    nn_r2=None):
+    """Forces on explicit sinks (positions xi [n_i x 3], velocities vi, order-6
+    accelerations ai); i_slot[k] >= 0 names the loaded slot that is sink k."""
+    ptrs, kind, _k = _marshal([i_slot, xi, vi, ai, acc, jerk, snap, pot, nn_id, nn_r2],
+                              [I4, F8, F8, F8, F8, F8, F8, F8, I4, F8])
+    _check(load().sp2_compute_ext(ctx, len(xi), *ptrs, kind), ctx)
 
 
 class sp2_block_stats(Structure):
@@ -374,6 +384,7 @@ class Context:
     def predict(self, t): return sp2_predict(self.ctx, t)
     def compute(self, *a, **k): return sp2_compute(self.ctx, *a, **k)
     def compute_nb(self, *a, **k): return sp2_compute_nb(self.ctx, *a, **k)
+    def compute_ext(self, *a, **k): return sp2_compute_ext(self.ctx, *a, **k)
     def get_j(self, *a, **k): return sp2_get_j(self.ctx, *a, **k)
     def block_init(self, *a): return sp2_block_init(self.ctx, *a)
     def block_run(self, *a): return sp2_block_run(self.ctx, *a)
