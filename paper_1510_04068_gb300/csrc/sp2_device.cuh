@@ -82,6 +82,12 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
+// Policies whose chunk fold reads the chunk's records (batched kernel).
+template <class P, class = void>
+struct has_fold_tile { static constexpr bool value = false; };
+template <class P>
+struct has_fold_tile<P, decltype(void(&P::fold_tile))> { static constexpr bool value = true; };
+
 // Policies that evaluate two sources per step define kPaired = true.
 template <class P, class = void>
 struct is_paired { static constexpr bool value = false; };
@@ -102,8 +108,8 @@ __device__ __forceinline__ void nn_merge(double &d, int &id, double od, int oid)
 // in FP32.  Sums are kept in two FP32 levels -- a partial over kChunk sources,
 // folded into a second FP32 level -- and the second level is added into
 // running totals once at least kFlush sources have passed (at a tile end in
-// the pass kernel): FP64 totals here (the batched kernel keeps them in
-// registers), double-single totals in shared memory in the paired policy.
+// the pass kernel): double-single totals in registers here (the batched
+// kernel), in shared memory in the paired policy.
 // Sequential FP32 summation rounds every add at the scale of the running sum,
 // so a long FP32 sum dominated by one large term loses ~sqrt(k) ulps; the two
 // short levels bound that error by ~(kChunk + sources per flush / kChunk) ulps.
@@ -130,10 +136,14 @@ struct MixedForce {
     };
     struct Acc {
         float f[NS];     // level 1: current chunk
-        float g[NS];     // level 2: chunks since the last FP64 flush
+        float g[NS];     // level 2: chunks since the last flush
+        float th[NS];    // running totals, double-single (hi, lo)
+        float tl[NS];
         unsigned ck;     // nearest-neighbour key of the current chunk
         unsigned bk;     // best key so far, and the slot of its chunk's first source
         int bbase;
+        float bd;        // nearest neighbour so far: exact r^2 and id (-1: none)
+        int bid;
     };
 
     __device__ static __forceinline__ Rec ld_shared(const unsigned char *p) {
@@ -181,9 +191,11 @@ struct MixedForce {
     }
     __device__ static __forceinline__ void init(Acc &c) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = 0.f;
+        for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = c.th[f] = c.tl[f] = 0.f;
         c.ck = c.bk = 0xffffffffu;
         c.bbase = -1;
+        c.bd = f_inf();
+        c.bid = -1;
     }
     // Squared distance between a record and the sink, exactly as interact() forms it.
     __device__ static __forceinline__ float dist2(const Rec &r, const Sink &s) {
@@ -254,43 +266,47 @@ struct MixedForce {
             c.ck = FIRST ? key : min(c.ck, key);
         }
     }
-    // end of a chunk whose first source (for this thread) is slot `base`
-    __device__ static __forceinline__ void fold(Acc &c, int base) {
+    // End of a chunk (batched kernel) whose records start at chunk (stride RB)
+    // in shared memory: a new nearest neighbour's exact r^2 and id are taken
+    // from its record there (filler records never qualify).
+    __device__ static __forceinline__ void fold_tile(Acc &c, int base, const unsigned char *chunk, const Sink &s) {
 #pragma unroll
         for (int f = 0; f < NS; ++f) c.g[f] += c.f[f];
         if (NN && c.ck < c.bk) {
             c.bk = c.ck;
             c.bbase = base;
+            if ((c.ck & ~kKeyMask) < 0x7f800000u) {
+                const Rec r = ld_shared(chunk + static_cast<int>(c.ck & kKeyMask) * RB);
+                c.bd = dist2(r, s);
+                c.bid = __float_as_int(r.w[1].w);
+            } else {
+                c.bd = f_inf();
+                c.bid = -1;
+            }
         }
     }
-    // level 2 -> FP64 totals tot[f * stride]
-    __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
+    // Level 2 -> the running totals, double-single (hi, lo) in registers,
+    // updated by TwoSum (Knuth): no FP64 arithmetic per flush.  The tot
+    // argument is not used.
+    __device__ static __forceinline__ void flush(Acc &c, double *, int) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) { tot[f * stride] += static_cast<double>(c.g[f]); c.g[f] = 0.f; }
+        for (int f = 0; f < NS; ++f) {
+            const float v = c.g[f];
+            const float h = c.th[f] + v;
+            const float bv = h - c.th[f];
+            c.tl[f] += (c.th[f] - (h - bv)) + (v - bv);
+            c.th[f] = h;
+            c.g[f] = 0.f;
+        }
     }
-    __device__ static __forceinline__ void zero_totals(double *tot, int stride) {
+    __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) tot[f * stride] = 0.0;
-    }
-    __device__ static __forceinline__ void totals(const Acc &, const double *tot, int stride, double *t) {
-#pragma unroll
-        for (int f = 0; f < NS; ++f) t[f] = tot[f * stride];
+        for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(c.th[f]) + static_cast<double>(c.tl[f]);
         t[NS - 1] = -t[NS - 1];
     }
-    // The chosen source is slot bbase + u * jl; its r^2 is recomputed exactly
-    // from its record.  limit: one past the last real source slot (filler
-    // records never qualify, the bound keeps the lookup inside the arrays).
-    __device__ static __forceinline__ void nn(const Acc &c, const Sink &s, const unsigned char *rec, int64_t limit,
-                                              int jl, double &d, int &id) {
-        const int64_t j = (c.bbase >= 0 && c.bk != 0xffffffffu) ? c.bbase + static_cast<int64_t>(c.bk & kKeyMask) * jl : -1;
-        if (NN && j >= 0 && j < limit && (c.bk & ~kKeyMask) < 0x7f800000u) {
-            const Rec r = ld_global(rec + j * RB);
-            d = static_cast<double>(dist2(r, s));
-            id = __float_as_int(r.w[1].w);
-        } else {
-            d = d_inf();
-            id = -1;
-        }
+    __device__ static __forceinline__ void nn_acc(const Acc &c, double &d, int &id) {
+        d = (NN && c.bid >= 0) ? static_cast<double>(c.bd) : d_inf();
+        id = NN ? c.bid : -1;
     }
     template <class Out>
     __device__ static __forceinline__ void write_final(const Out &o, int64_t i, const double *t, double d, int id) {
@@ -1524,7 +1540,8 @@ __device__ __forceinline__ void batch_tile_loop(const unsigned char *st, int tb,
                 const typename P::Rec r = P::ld_shared(st + (q0 + u) * P::RB);
                 P::template interact<SELF, false>(r, tb + q0 + u, u, sk, ac, eps2);
             }
-            P::fold(ac, tb + q0);
+            if constexpr (has_fold_tile<P>::value) P::fold_tile(ac, tb + q0, st + q0 * P::RB, sk);
+            else P::fold(ac, tb + q0);
         }
     }
 }
@@ -1532,8 +1549,8 @@ __device__ __forceinline__ void batch_tile_loop(const unsigned char *st, int tb,
 // Warps take (system, up-to-32-sink chunk) items from the device queue in the
 // plan's cost order; one sink per lane.  The system's sources pass through a
 // warp-private shared-memory tile filled with coalesced 16-byte loads (ragged
-// ends padded with filler records), then are read as broadcasts.  FP64 totals
-// stay in registers (systems are short).
+// ends padded with filler records), then are read as broadcasts.  The running
+// totals stay in registers (systems are short).
 template <class P>
 __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams b) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1596,7 +1613,8 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
         P::totals(ac, tot, 1, t);
         double nd;
         int nid;
-        P::nn(ac, sk, b.rec, static_cast<int64_t>(it.x) + it.y, 1, nd, nid);
+        if constexpr (has_fold_tile<P>::value) P::nn_acc(ac, nd, nid);
+        else P::nn(ac, sk, b.rec, static_cast<int64_t>(it.x) + it.y, 1, nd, nid);
         if (val) P::write_final(b, static_cast<int64_t>(slot) - b.out_base, t, nd, nid);
     }
 }
