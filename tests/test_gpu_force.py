@@ -201,3 +201,17 @@ def test_in_pass_reduction_levels(sp2, oracle_mod, mixed, n_i, split):
     g = gpu_run(sp2, s, idx, order=4, precision=sp2.SP2_MIXED if mixed else sp2.SP2_FP64, eps2=eps2, launch=launch)
     r = oracle_ref(oracle_mod, s, idx, order=4, eps2=eps2)
     check(g, r, order=4, mixed=mixed, s=s, i_idx=idx, label=f"split={split}")
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_mixed_far_from_origin(sp2, oracle_mod, order):
+    """Double-single positions: a Plummer sphere moved 10^4 length units away
+    (FP32 alone would keep ~3 significant digits of the close-pair
+    separations) still meets the mixed-precision tolerances."""
+    n, eps2 = 3000, 1e-8
+    s = state(n, 33, order=order)
+    s["x"] = s["x"] + np.array([1.0e4, -3.7e3, 2.2e3])
+    idx = np.sort(np.random.default_rng(3).choice(n, 400, replace=False)).astype(np.int32)
+    g = gpu_run(sp2, s, idx, order=order, precision=sp2.SP2_MIXED, eps2=eps2)
+    r = oracle_ref(oracle_mod, s, idx, order=order, eps2=eps2)
+    check(g, r, order=order, mixed=True, s=s, i_idx=idx, label="far from origin")
