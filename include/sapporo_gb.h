@@ -258,6 +258,14 @@ sp2_status sp2_get_j(sp2_ctx *ctx, int64_t first, int64_t n, double *x, double *
  *   the last step and dt_max, dividing t1.  Afterwards every particle is at
  *   its own t_i <= t_end (all at t_end when t_end is a multiple of dt_max).
  *   Statistics go to *stats (may be NULL).
+ *   Execution: the block time, the active count and a stop flag stay on the
+ *   device; blocks are queued 32 at a time (the first 32 as plain launches,
+ *   the rest by replaying one captured CUDA graph of 32 blocks) and the host
+ *   reads the state once per 32 blocks.  A block past t_end makes the rest of
+ *   its batch do nothing.  The force pass takes its shape (lanes per sink,
+ *   source split) from the active count on the device.  Runs on the context's
+ *   stream and returns after synchronising it; a stream that cannot be
+ *   captured gets plain launches throughout.
  * Errors: SP2_ERR_UNSUPPORTED (order), SP2_ERR_STATE (nothing loaded, or
  * block_run without block_init after the last sp2_set_j), SP2_ERR_ARG. */
 typedef struct {

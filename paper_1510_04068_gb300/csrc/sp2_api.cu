@@ -73,6 +73,7 @@ struct sp2_ctx {
     int32_t *noslot = nullptr;              // -1 per explicit sink (no self pair)
     size_t sinkrec_cap = 0, noslot_cap = 0;
     double *blk_dt = nullptr;               // block time-steps: per-slot step
+    BlockDev *blk_dev = nullptr;            // block time-steps: device-driven run state
     int32_t *blk_active = nullptr;          // block time-steps: active slots
     size_t blk_dt_cap = 0, blk_active_cap = 0;
     bool blk_ready = false;                 // sp2_block_init has run since the last set_j
@@ -283,7 +284,7 @@ size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int thr
 sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const unsigned char *rec, int rb,
                     int64_t n_valid, const int32_t *i_idx, int64_t n_i, int64_t j_begin, int64_t j_end,
                     const PassOut &o, const sp2_launch *forced, int stage_force, float *ms_out = nullptr,
-                    bool allow_fused = false) {
+                    bool allow_fused = false, const unsigned int *n_i_dev = nullptr) {
     if (n_i <= 0) return SP2_OK;
     sp2_launch L;
     if (forced) {
@@ -299,9 +300,14 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     int tile = L.j_tile;
     const int64_t sinks_per_cta = static_cast<int64_t>(L.threads / jl) * L.i_per_thread;
     const int64_t n_iblk = ceil_div(n_i, sinks_per_cta);
-    const int fused = (allow_fused && kind == K_FORCE && mixed && c->js.dsc && n_iblk == 1) ? 1 : 0;
-    if (!fused && allow_fused) SP2_CKS(materialize(c));
-    KernelKey key{kind, order, mixed, nn, L.i_per_thread, fused, nb};
+    // n_i_dev: the sink count is chosen on the device (n_i is its bound); the
+    // caller has written the records
+    const int fused = (!n_i_dev && allow_fused && kind == K_FORCE && mixed && c->js.dsc && n_iblk == 1) ? 1 : 0;
+    if (!fused && allow_fused && !n_i_dev) SP2_CKS(materialize(c));
+    const int devn = n_i_dev ? 1 : 0;
+    if (devn && (kind != K_FORCE || order != 4 || nn || nb || L.i_per_thread != 1))
+        return fail(c, SP2_ERR_UNSUPPORTED, "device-count passes are order-4 forces without neighbours");
+    KernelKey key{kind, order, mixed, nn, L.i_per_thread, fused, nb, devn};
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
@@ -316,12 +322,16 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         if (per_sm <= 0) return fail(c, SP2_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
     }
     const int64_t n_items = n_iblk * split;
-    const int grid = static_cast<int>(std::min<int64_t>(n_items, static_cast<int64_t>(c->sm_count) * per_sm));
-    const int static_items = (grid == n_items) ? 1 : 0;  // one wave: CTA b takes item b
+    // a device-count pass may make more work items than the host's bound
+    // shows: it takes every resident CTA
+    const int64_t resident = static_cast<int64_t>(c->sm_count) * per_sm;
+    const int grid = static_cast<int>(devn ? resident : std::min<int64_t>(n_items, resident));
+    const int static_items = (!n_i_dev && grid == n_items) ? 1 : 0;  // one wave: CTA b takes item b
 
     ForceParams p{};
     p.rec = rec;
     p.i_idx = i_idx;
+    p.n_i_dev = n_i_dev;
     p.n_i = n_i;
     p.j_begin = j_begin;
     p.j_end = j_end;
@@ -363,10 +373,15 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         p.part_id = c->part_id;
         p.sink_major = split >= kWarpReduceMinSplit ? 1 : 0;
         // fuse the reduction into the pass when one CTA's share of it is small
+        // (a device-count pass always does; its i-blocks may be as small as
+        // threads / 32 sinks)
+        if (devn && sinks_per_cta * split > kFusedReduceMaxValues)
+            return fail(c, SP2_ERR_UNSUPPORTED, "device-count pass: split too large for the in-pass reduction");
         if (std::min<int64_t>(sinks_per_cta, n_i) * split <= kFusedReduceMaxValues) {
+            const int64_t blocks = devn ? ceil_div(n_i, std::max(1, L.threads / 32)) : n_iblk;
             const size_t old_cap = c->done_cap;
             SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->done), &c->done_cap,
-                           static_cast<size_t>(n_iblk) * sizeof(unsigned int), "reduction-counter"));
+                           static_cast<size_t>(blocks) * sizeof(unsigned int), "reduction-counter"));
             if (c->done_cap != old_cap) SP2_CK(c, cudaMemsetAsync(c->done, 0, c->done_cap, c->stream));
             p.fused_reduce = 1;
             p.done = c->done;
@@ -1129,44 +1144,111 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
     const int64_t n = c->n_loaded;
     const int mixed = c->cfg.precision == SP2_MIXED;
     double *a1 = c->tmp, *j1 = c->tmp + 3 * c->cfg.n_max;
-    unsigned int *count = c->dev_words + 6;
-    unsigned long long *t1bits = reinterpret_cast<unsigned long long *>(c->dev_words + 8);
-    sp2_block_stats acc{};
-    acc.min_active = INT64_MAX;
-    acc.t = -1.0;
-    for (;;) {
-        ev_begin(c, ST_OTHER);
-        SP2_CK(c, launch_block_select(c->js.t, c->blk_dt, n, t1bits, c->blk_active, count, c->stream));
-        ev_end(c, ST_OTHER);
-        unsigned int hw[4];
-        SP2_CK(c, cudaMemcpyAsync(hw, c->dev_words + 6, sizeof hw, cudaMemcpyDeviceToHost, c->stream));
-        SP2_CK(c, cudaStreamSynchronize(c->stream));
-        c->launches += 2;
-        unsigned long long bits = static_cast<unsigned long long>(hw[2]) | (static_cast<unsigned long long>(hw[3]) << 32);
-        double t1;
-        std::memcpy(&t1, &bits, sizeof t1);
-        const int64_t n_act = hw[0];
-        if (!(t1 <= t_end) || n_act == 0) break;
-        SP2_CKS(sp2_predict(c, t1));
-        PassOut o;
-        o.acc = a1;
-        o.jerk = j1;
-        SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec, c->rb, n, c->blk_active, n_act, 0, n, o, nullptr, ST_FORCE,
-                         nullptr, true));
-        ev_begin(c, ST_OTHER);
-        SP2_CK(c, launch_block_correct(c->js, c->blk_dt, c->blk_active, n_act, t1, a1, j1, eta, dt_max, c->stream));
-        ev_end(c, ST_OTHER);
-        c->launches += 1;
-        c->rec_valid = false;
-        acc.block_steps += 1;
-        acc.active_sum += n_act;
-        acc.max_active = std::max(acc.max_active, n_act);
-        acc.min_active = std::min(acc.min_active, n_act);
-        acc.t = t1;
+    if (!c->blk_dev) {
+        c->blk_dev = static_cast<BlockDev *>(dalloc(c, sizeof(BlockDev)));
+        if (!c->blk_dev) return fail(c, SP2_ERR_NOMEM, "cannot allocate the block-step state");
     }
-    SP2_CK(c, cudaStreamSynchronize(c->stream));
-    if (acc.block_steps == 0) acc.min_active = 0;
-    if (st) *st = acc;
+    BlockDev h{};
+    h.min_active = 0xffffffffu;
+    h.t_last = -1.0;
+    SP2_CK(c, cudaMemcpyAsync(c->blk_dev, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    // The active count is only known on the device: the pass kernel derives
+    // its sinks per CTA and source split from it.  The host fixes the CTA
+    // (256 threads, one sink per thread), the tile (256 sources, room for 32
+    // lanes per sink) and the largest split, so that one CTA's share of the
+    // in-pass reduction stays bounded and the partial sums of all n sinks fit
+    // 256 MB.
+    sp2_launch L{};
+    L.threads = 256;
+    L.i_per_thread = 1;
+    L.j_lanes = 1;
+    L.j_tile = 256;
+    L.split_j = static_cast<int>(kFusedReduceMaxValues / L.threads);
+    while (L.split_j > 1 && static_cast<double>(n) * 8.0 * 8.0 * L.split_j > 256.0 * (1 << 20)) L.split_j /= 2;
+    {
+        KernelKey key{K_FORCE, 4, mixed, 0, 1, 0, 0, 1};
+        int per_sm = 0;
+        SP2_CK(c, force_kernel_occupancy(key, L.threads, L.j_tile, &per_sm));
+        if (per_sm <= 0) return fail(c, SP2_ERR_UNSUPPORTED, "block-step pass does not fit on an SM");
+        L.ctas_per_sm = per_sm;
+    }
+    PassOut o;
+    o.acc = a1;
+    o.jerk = j1;
+    // Blocks are queued in batches; a block past t_end sets the stop flag on
+    // the device and every later kernel of the batch does nothing.  The first
+    // batch is launched directly (it sizes the pass buffers); the rest replay
+    // one captured batch as a CUDA graph.
+    constexpr int kBatch = 32;
+    auto enqueue = [&]() -> sp2_status {
+        for (int k = 0; k < kBatch; ++k) {
+            ev_begin(c, ST_OTHER);
+            SP2_CK(c, launch_block_begin(c->blk_dev, c->js.t, c->blk_dt, n, t_end, c->blk_active, c->stream));
+            ev_end(c, ST_OTHER);
+            ev_begin(c, ST_PREDICT);
+            SP2_CK(c, launch_predict(4, mixed, c->js, n, 0.0, c->rec, c->stream, c->blk_dev));
+            ev_end(c, ST_PREDICT);
+            SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec, c->rb, n, c->blk_active, n, 0, n, o, &L, ST_FORCE,
+                             nullptr, false, &c->blk_dev->count));
+            ev_begin(c, ST_OTHER);
+            SP2_CK(c, launch_block_correct_dev(c->js, c->blk_dt, c->blk_active, n, c->blk_dev, a1, j1, eta, dt_max,
+                                               c->stream));
+            ev_end(c, ST_OTHER);
+            c->launches += 5;  // run_pass counts the force kernel
+        }
+        return SP2_OK;
+    };
+    auto read_state = [&]() -> sp2_status {
+        SP2_CK(c, cudaMemcpyAsync(&h, c->blk_dev, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+        SP2_CK(c, cudaStreamSynchronize(c->stream));
+        return SP2_OK;
+    };
+    SP2_CKS(enqueue());
+    SP2_CKS(read_state());
+    // a stream that cannot be captured (the legacy default stream) keeps
+    // direct launches
+    if (!h.stop && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        while (!h.stop) {
+            SP2_CKS(enqueue());
+            SP2_CKS(read_state());
+        }
+    }
+    if (!h.stop) {
+        const int64_t per_batch = c->launches;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        c->capturing = true;
+        const sp2_status se = enqueue();
+        c->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (se != SP2_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return se;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        SP2_CK(c, e);
+        const int64_t batch_launches = c->launches - per_batch;
+        sp2_status rs = SP2_OK;
+        while (!h.stop && rs == SP2_OK) {
+            e = cudaGraphLaunch(exec, c->stream);
+            if (e != cudaSuccess) break;
+            c->launches += batch_launches;
+            rs = read_state();
+        }
+        cudaGraphExecDestroy(exec);
+        SP2_CK(c, e);
+        if (rs != SP2_OK) return rs;
+    }
+    c->rec_valid = false;
+    if (st) {
+        st->block_steps = static_cast<int64_t>(h.steps);
+        st->active_sum = static_cast<int64_t>(h.active_sum);
+        st->max_active = h.max_active;
+        st->min_active = h.steps ? h.min_active : 0;
+        st->t = h.t_last;
+    }
     return SP2_OK;
 }
 

@@ -539,6 +539,7 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
 // ---------------------------------------------------------------------------
 template <int ORDER, bool NN>
 struct Fp64Force {
+    static constexpr int kOrder = ORDER;
     static constexpr int NW = (ORDER == 6) ? 6 : 4;
     static constexpr bool kCanFuse = false;
     static constexpr int RB = NW * 16;
@@ -1247,7 +1248,7 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
 // double-single pair in the paired policy), [sink k][field f][thread]
 // so each thread owns its slots.
 template <class P, int IPT, bool FUSED>
-__global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
+__device__ __forceinline__ void pass_body(const ForceParams &p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_item;
     const int tid = threadIdx.x;
@@ -1435,6 +1436,55 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
             *p.exit_count = 0u;
             __threadfence();
         }
+    }
+}
+
+// Device-count form (block time-steps): the sink count is read from device
+// memory, written there by the kernel that chose the active set, and every
+// CTA derives the launch shape from it, with the launch's threads and tile,
+// and the host's source split as an upper bound (it sized the partial-sum
+// buffers and the reduction counters).  Sources are cut into slices of at
+// least one tile; lanes share a sink (j_lanes) while the sinks do not fill a
+// CTA or the (i-block, slice) items do not cover the grid; then the split
+// aims at ~4 items per CTA.
+__device__ __forceinline__ void device_shape(ForceParams &q) {
+    const int nt = blockDim.x;
+    const int64_t n_i = *q.n_i_dev;
+    const int64_t n_j = q.j_end - q.j_begin;
+    int64_t cap = n_j / q.tile;
+    if (cap > q.split) cap = q.split;
+    if (cap < 1) cap = 1;
+    int jl = 1;
+    while (jl < 32 && jl * 8 < q.tile) {
+        const int64_t spc = nt / jl;
+        if (spc <= n_i && (n_i + spc - 1) / spc * cap >= gridDim.x) break;
+        jl *= 2;
+    }
+    const int spc = nt / jl;
+    const int64_t n_iblk = (n_i + spc - 1) / spc;
+    int64_t split = n_iblk > 0 ? (4 * static_cast<int64_t>(gridDim.x) + n_iblk - 1) / n_iblk : 1;
+    if (split > cap) split = cap;
+    if (split < 1) split = 1;
+    const int64_t per_slice = (n_j + split - 1) / split;
+    q.slice_len = (per_slice + q.tile - 1) / q.tile * q.tile;
+    q.split = static_cast<int>((n_j + q.slice_len - 1) / q.slice_len);
+    q.n_i = n_i;
+    q.n_iblk = n_iblk;
+    q.n_items = n_iblk * q.split;
+    q.sinks_per_cta = spc;
+    q.jl = jl;
+    q.sink_major = q.split >= kWarpReduceMinSplit ? 1 : 0;
+}
+
+template <class P, int IPT, bool FUSED, bool DEVN = false>
+__global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
+    if constexpr (DEVN) {
+        static_assert(IPT == 1 && !FUSED, "the device-count form takes one sink per thread");
+        ForceParams q = p;
+        device_shape(q);
+        pass_body<P, IPT, FUSED>(q);
+    } else {
+        pass_body<P, IPT, FUSED>(p);
     }
 }
 
@@ -1635,33 +1685,42 @@ inline size_t pass_smem(size_t tile, int threads) {
 
 constexpr int kMaxDynSmem = 200 * 1024;
 
-template <class P, int IPT, bool FUSED>
+template <class P, int IPT, bool FUSED, bool DEVN = false>
 inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t tile, cudaStream_t s) {
     static bool attr_set = false;
     const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) return cudaErrorInvalidConfiguration;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxDynSmem);
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED, DEVN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    pass_kernel<P, IPT, FUSED><<<grid, threads, smem, s>>>(p);
+    pass_kernel<P, IPT, FUSED, DEVN><<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <class P, int IPT, bool FUSED>
+template <class P, int IPT, bool FUSED, bool DEVN = false>
 inline cudaError_t occupancy_pass(int threads, size_t tile, int *blocks) {
     const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads);
     if (smem > static_cast<size_t>(kMaxDynSmem)) {
         *blocks = 0;
         return cudaSuccess;
     }
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED, DEVN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxDynSmem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT, FUSED>, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT, FUSED, DEVN>, threads, smem);
 }
+
+// The device-count pass (block time-steps) exists for the order-4 force
+// policies without nearest neighbours, one sink per thread.
+template <class P>
+struct takes_device_count { static constexpr bool value = false; };
+template <>
+struct takes_device_count<MixedPairForce<4, false>> { static constexpr bool value = true; };
+template <>
+struct takes_device_count<Fp64Force<4, false>> { static constexpr bool value = true; };
 
 template <class P, bool FUSED>
 inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
@@ -1677,7 +1736,16 @@ inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int g
 // fused = 1 is available for the mixed force policies only
 template <class P>
 inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                                cudaStream_t s, int *blocks, int fused = 0) {
+                                cudaStream_t s, int *blocks, int fused = 0, int devn = 0) {
+    if constexpr (takes_device_count<P>::value) {
+        if (devn) {
+            if (ipt != 1 || fused) return cudaErrorInvalidValue;
+            return occ ? occupancy_pass<P, 1, false, true>(threads, tile, blocks)
+                       : launch_pass<P, 1, false, true>(*p, grid, threads, tile, s);
+        }
+    } else {
+        if (devn) return cudaErrorInvalidValue;
+    }
     if constexpr (P::kCanFuse && is_paired<P>::value) {
         if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, tile, s, blocks);
     } else {
@@ -1743,9 +1811,9 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
                                                                            tile, s, nullptr, k.fused)      \
                         : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, tile, s, nullptr,  \
-                                                        k.fused)                                           \
+                                                        k.fused, k.devn)                                   \
                     : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, tile, s, nullptr, \
-                                                         k.fused);                                         \
+                                                         k.fused, k.devn);                                 \
     }                                                                                                      \
     cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t tile, int *blocks) {       \
         if (k.nb)                                                                                          \
@@ -1753,9 +1821,9 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
                                                                            tile, 0, blocks, k.fused)       \
                         : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks,  \
-                                                        k.fused)                                           \
+                                                        k.fused, k.devn)                                   \
                     : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks, \
-                                                         k.fused);                                         \
+                                                         k.fused, k.devn);                                 \
     }                                                                                                      \
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {        \
         return k.nn ? launch_reduce<POLICY<ORDER, true>>(r, s) : launch_reduce<POLICY<ORDER, false>>(r, s); \

@@ -43,6 +43,7 @@ inline int vjp_record_bytes(int mixed) { return mixed ? 80 : 112; }
 struct ForceParams {
     const unsigned char *rec;  // predicted records, slot 0
     const int32_t *i_idx;      // sink slots (n_i); with sink_rec: slot for the self pair, or < 0 for none
+    const unsigned int *n_i_dev;  // if set: the sink count is read here (n_i is then only its upper bound)
     const unsigned char *sink_rec;  // explicit sinks: record of sink position i (null: sinks are rec[i_idx[i]])
     int64_t n_i;
     int64_t j_begin, j_end;    // source slots [j_begin, j_end)
@@ -134,6 +135,7 @@ struct KernelKey {
     int ipt;    // 1 / 2 / 4
     int fused;  // 1: predict sources in the pass (mixed force only)
     int nb;     // 1: neighbour lists (force kernels with nearest neighbour, ipt 1)
+    int devn;   // 1: sink count read on the device, shape derived from it (order 4, no NN, ipt 1)
 };
 
 // Each kernel translation unit provides these for its (order, precision).
@@ -171,10 +173,21 @@ cudaError_t launch_scatter_j(const JStore &dst, const int32_t *slots, int64_t n,
                              unsigned int *err, const int32_t *id, const double *m, const double *x,
                              const double *v, const double *a, const double *jk, const double *sn,
                              const double *t, cudaStream_t s);
+// State of a device-driven block time-step run (one per context).
+struct BlockDev {
+    unsigned long long t1bits;  // order-preserving key of the current block time
+    unsigned int count;         // active particles of the current block (0: none / stopped)
+    unsigned int stop;          // set once the next block time passes t_end
+    unsigned long long steps, active_sum;
+    unsigned int max_active, min_active;
+    double t_last;              // time of the last block taken
+};
+
 // Mixed records come from js.dsc when it is set (double-single arithmetic),
-// from the FP64 arrays otherwise.
+// from the FP64 arrays otherwise.  t_dev: if set, the time is read on the
+// device from a BlockDev (the launch does nothing when its count is zero)
 cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, double t,
-                           unsigned char *rec, cudaStream_t s);
+                           unsigned char *rec, cudaStream_t s, const BlockDev *t_dev = nullptr);
 // Refresh js.dsc for slots [first, first + n) from the FP64 store.
 cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n, cudaStream_t s);
 // (m, x, v) -> order-4 records with no prediction (all-pairs entry points)
@@ -184,14 +197,18 @@ cudaError_t launch_pack_state(int mixed, int64_t n, const double *m, const doubl
 cudaError_t launch_pack_sinks(int order, int mixed, int64_t n, const double *x, const double *v, const double *a,
                               unsigned char *rec, cudaStream_t s);
 cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
+
 // Block time-steps (Hermite-4 with individual power-of-two steps).
 cudaError_t launch_block_init(const JStore &js, double *dt, int64_t n, double eta_s, double dt_max, double t0,
                               cudaStream_t s);
-// *t1bits = bits of min(t + dt); active[0 .. *count) = slots with t + dt == t1
-cudaError_t launch_block_select(const double *t, const double *dt, int64_t n, unsigned long long *t1bits,
-                                int32_t *active, unsigned int *count, cudaStream_t s);
-cudaError_t launch_block_correct(const JStore &js, double *dt, const int32_t *active, int64_t n_act, double t1,
-                                 const double *a1, const double *j1, double eta, double dt_max, cudaStream_t s);
+// bd->t1bits = key of t1 = min(t + dt); active[0 .. bd->count) = slots with
+// t + dt == t1, or bd->stop set (count 0) once t1 > t_end
+cudaError_t launch_block_begin(BlockDev *bd, const double *t, const double *dt, int64_t n, double t_end,
+                               int32_t *active, cudaStream_t s);
+// Hermite-4 corrector and new step of the active slots of the current block
+cudaError_t launch_block_correct_dev(const JStore &js, double *dt, const int32_t *active, int64_t n_max,
+                                     BlockDev *bd, const double *a1, const double *j1, double eta, double dt_max,
+                                     cudaStream_t s);
 cudaError_t launch_nb_finish(const int32_t *ids, int64_t n_i, int nb_max, const int32_t *count, int32_t *list,
                              cudaStream_t s);
 cudaError_t launch_h4_predict_pack(int mixed, int64_t n, double dt, const double *m,

@@ -78,11 +78,30 @@ __global__ void dscache_kernel(JStore d, int64_t first, int64_t n) {
     if (k < n) write_dscache(d, first + k);
 }
 
+// Block times are compared through an unsigned key that orders like the
+// doubles (negative times included): the sign bit flipped for t >= 0, every bit
+// for t < 0; all ones (the empty minimum) decodes to NaN.
+__device__ __forceinline__ unsigned long long time_key(double t) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(t));
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_time(unsigned long long k) {
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
 // Mixed-precision predictor on the double-single cache (predict_ds_record).
 template <int ORDER>
-__global__ void predict_ds_kernel(const float4 *dsc, int64_t n, float t_hi, float t_lo, unsigned char *rec) {
+__global__ void predict_ds_kernel(const float4 *dsc, int64_t n, float t_hi, float t_lo, unsigned char *rec,
+                                  const BlockDev *bd) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if (bd) {  // time of the current block, chosen on the device
+        if (bd->count == 0) return;
+        const double t = key_time(bd->t1bits);
+        t_hi = __double2float_rn(t);
+        t_lo = __double2float_rn(t - static_cast<double>(t_hi));
+    }
     float4 o[4];
     predict_ds_record<ORDER>(dsc, j, t_hi, t_lo, o);
     float4 *dst = reinterpret_cast<float4 *>(rec + j * (ORDER == 6 ? 64 : 48));
@@ -116,9 +135,13 @@ __global__ void scatter_kernel(JStore d, const int32_t *slots, int64_t n, int64_
 }
 
 template <int ORDER, bool MIXED>
-__global__ void predict_kernel(JStore js, int64_t n, double t, unsigned char *rec) {
+__global__ void predict_kernel(JStore js, int64_t n, double t, unsigned char *rec, const BlockDev *bd) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if (bd) {
+        if (bd->count == 0) return;
+        t = key_time(bd->t1bits);
+    }
     const double c2 = 0.5, c3 = 1.0 / 6.0, c4 = 1.0 / 24.0;
     const double dt = dadd(t, -js.t[j]);
     const double dt2 = dmul(dt, dt);
@@ -219,33 +242,11 @@ __global__ void block_init_kernel(JStore js, double *dt, int64_t n, double eta_s
     js.t[s] = t0;
 }
 
-// min over particles of t_i + dt_i, as the bits of a non-negative double
-__global__ void block_next_kernel(const double *t, const double *dt, int64_t n, unsigned long long *out) {
-    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    unsigned long long v = ~0ull;
-    if (s < n) v = static_cast<unsigned long long>(__double_as_longlong(t[s] + dt[s]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
-    if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(out, v);
-}
-
-// slots whose next time is t1 (the active block), appended in any order
-__global__ void block_active_kernel(const double *t, const double *dt, int64_t n, const unsigned long long *t1bits,
-                                    int32_t *active, unsigned int *count) {
-    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    if (t[s] + dt[s] == __longlong_as_double(static_cast<long long>(*t1bits)))
-        active[atomicAdd(count, 1u)] = static_cast<int32_t>(s);
-}
-
 // Hermite-4 corrector and the next step for the active particles (a1, j1 at
 // the predicted state, position k of the active list); the double-single
 // cache follows the store.
-__global__ void block_correct_kernel(JStore js, double *dt, const int32_t *active, int64_t n_act, double t1,
-                                     const double *a1, const double *j1, double eta, double dt_max) {
-    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (k >= n_act) return;
-    const int64_t s = active[k];
+__device__ __forceinline__ void correct_one(const JStore &js, double *dt, int64_t s, int64_t k, double t1,
+                                            const double *a1, const double *j1, double eta, double dt_max) {
     const double h = t1 - js.t[s];
     const double h2 = h * h;
     double a2[3], a3[3], an[3], jn[3];
@@ -273,6 +274,7 @@ __global__ void block_correct_kernel(JStore js, double *dt, const int32_t *activ
     if (js.dsc) write_dscache(js, s);
 }
 
+
 // Explicit sinks (sp2_compute_ext): positions / velocities [/ accelerations]
 // given by the caller, packed in the context's record format.
 template <int ORDER, bool MIXED>
@@ -288,6 +290,54 @@ __global__ void pack_sinks_kernel(int64_t n, const double *x, const double *v, c
     const int rb = MIXED ? (ORDER == 6 ? 64 : 48) : (ORDER == 6 ? 96 : 64);
     if (MIXED) store_mixed(rec, rb, j, xp, vp, ORDER == 6 ? ap : nullptr, 0.0, -1);
     else store_fp64(rec, rb, j, xp, vp, ORDER == 6 ? ap : nullptr, 0.0, -1);
+}
+
+// ---- the same block time-steps driven from the device: the block time,
+// the active count and a stop flag live in a BlockDev, so the host can queue
+// many blocks without reading anything back.
+__global__ void block_begin_kernel(BlockDev *bd) {
+    bd->count = 0u;
+    if (!bd->stop) bd->t1bits = ~0ull;
+}
+
+__global__ void block_next_dev_kernel(const double *t, const double *dt, int64_t n, BlockDev *bd) {
+    if (bd->stop) return;
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    unsigned long long v = ~0ull;
+    if (s < n) v = static_cast<unsigned long long>(time_key(t[s] + dt[s]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(&bd->t1bits, v);
+}
+
+// active set of the block, unless the block time has passed t_end (then the
+// run stops: count stays 0 and every later kernel of the run does nothing)
+__global__ void block_active_dev_kernel(const double *t, const double *dt, int64_t n, double t_end, BlockDev *bd,
+                                        int32_t *active) {
+    if (bd->stop) return;
+    const double t1 = key_time(bd->t1bits);
+    if (!(t1 <= t_end)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) bd->stop = 1u;
+        return;
+    }
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s < n && t[s] + dt[s] == t1) active[atomicAdd(&bd->count, 1u)] = static_cast<int32_t>(s);
+}
+
+__global__ void block_correct_dev_kernel(JStore js, double *dt, const int32_t *active, BlockDev *bd, const double *a1,
+                                         const double *j1, double eta, double dt_max) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const unsigned int n_act = bd->count;
+    const double t1 = key_time(bd->t1bits);
+    if (k == 0 && n_act > 0) {
+        bd->steps += 1;
+        bd->active_sum += n_act;
+        bd->max_active = max(bd->max_active, n_act);
+        bd->min_active = min(bd->min_active, n_act);
+        bd->t_last = t1;
+    }
+    if (k >= n_act) return;
+    correct_one(js, dt, active[k], k, t1, a1, j1, eta, dt_max);
 }
 
 __global__ void iota_kernel(int32_t *dst, int64_t n) {
@@ -425,26 +475,26 @@ cudaError_t launch_dscache(int order, const JStore &js, int64_t first, int64_t n
 }
 
 cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, double t, unsigned char *rec,
-                           cudaStream_t s) {
+                           cudaStream_t s, const BlockDev *bd) {
     if (n <= 0) return cudaSuccess;
     const unsigned g = grid_for(n);
     if (mixed && js.dsc) {
         const float th = static_cast<float>(t);
         const float tl = static_cast<float>(t - static_cast<double>(th));
-        if (order == 6) predict_ds_kernel<6><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
-        else if (order == 2) predict_ds_kernel<2><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
-        else predict_ds_kernel<4><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec);
+        if (order == 6) predict_ds_kernel<6><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec, bd);
+        else if (order == 2) predict_ds_kernel<2><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec, bd);
+        else predict_ds_kernel<4><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec, bd);
         return cudaGetLastError();
     }
     if (order == 6) {
-        if (mixed) predict_kernel<6, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
-        else predict_kernel<6, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
+        if (mixed) predict_kernel<6, true><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
+        else predict_kernel<6, false><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
     } else if (order == 2) {
-        if (mixed) predict_kernel<2, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
-        else predict_kernel<2, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
+        if (mixed) predict_kernel<2, true><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
+        else predict_kernel<2, false><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
     } else {
-        if (mixed) predict_kernel<4, true><<<g, kThreads, 0, s>>>(js, n, t, rec);
-        else predict_kernel<4, false><<<g, kThreads, 0, s>>>(js, n, t, rec);
+        if (mixed) predict_kernel<4, true><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
+        else predict_kernel<4, false><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
     }
     return cudaGetLastError();
 }
@@ -477,27 +527,26 @@ cudaError_t launch_iota(int32_t *dst, int64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_block_begin(BlockDev *bd, const double *t, const double *dt, int64_t n, double t_end,
+                               int32_t *active, cudaStream_t s) {
+    block_begin_kernel<<<1, 1, 0, s>>>(bd);
+    block_next_dev_kernel<<<grid_for(n), kThreads, 0, s>>>(t, dt, n, bd);
+    block_active_dev_kernel<<<grid_for(n), kThreads, 0, s>>>(t, dt, n, t_end, bd, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_correct_dev(const JStore &js, double *dt, const int32_t *active, int64_t n_max,
+                                     BlockDev *bd, const double *a1, const double *j1, double eta, double dt_max,
+                                     cudaStream_t s) {
+    if (n_max <= 0) return cudaSuccess;
+    block_correct_dev_kernel<<<grid_for(n_max), kThreads, 0, s>>>(js, dt, active, bd, a1, j1, eta, dt_max);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_init(const JStore &js, double *dt, int64_t n, double eta_s, double dt_max, double t0,
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     block_init_kernel<<<grid_for(n), kThreads, 0, s>>>(js, dt, n, eta_s, dt_max, t0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_block_select(const double *t, const double *dt, int64_t n, unsigned long long *t1bits,
-                                int32_t *active, unsigned int *count, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(t1bits, 0xff, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    block_next_kernel<<<grid_for(n), kThreads, 0, s>>>(t, dt, n, t1bits);
-    block_active_kernel<<<grid_for(n), kThreads, 0, s>>>(t, dt, n, t1bits, active, count);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_block_correct(const JStore &js, double *dt, const int32_t *active, int64_t n_act, double t1,
-                                 const double *a1, const double *j1, double eta, double dt_max, cudaStream_t s) {
-    if (n_act <= 0) return cudaSuccess;
-    block_correct_kernel<<<grid_for(n_act), kThreads, 0, s>>>(js, dt, active, n_act, t1, a1, j1, eta, dt_max);
     return cudaGetLastError();
 }
 

@@ -22,12 +22,12 @@ def sp2():
     return mod
 
 
-def _gpu_run(sp2, precision, m, x, v, eps2, t_end, eta, eta_s, dt_max):
+def _gpu_run(sp2, precision, m, x, v, eps2, t_end, eta, eta_s, dt_max, t0=0.0):
     n = len(m)
     c = sp2.Context(order=4, precision=precision, n_max=n, eps2=eps2, with_nn=0)
     z = np.zeros((n, 3))
-    c.set_j(0, np.arange(n, dtype=np.int32), m, x, v, z, z, None, np.zeros(n))
-    c.block_init(0.0, eta_s, dt_max)
+    c.set_j(0, np.arange(n, dtype=np.int32), m, x, v, z, z, None, np.full(n, t0))
+    c.block_init(t0, eta_s, dt_max)
     st = c.block_run(t_end, eta, dt_max)
     xs, vs, ts = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
     c.get_j(0, n, x=xs, v=vs, t=ts)
@@ -84,3 +84,20 @@ def test_block_run_in_stages_and_rules(sp2, oracle_mod):
     with pytest.raises(sp2.SP2Error):  # order 4 only
         c.block_init(0.0, 0.01, 2.0 ** -6)
     c.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_block_run_shift_in_time(sp2, mixed):
+    """The scheme depends on time only through differences and through the
+    commensurability of the steps: a run from t0 = -1/32 (a multiple of the
+    largest step) to 1/32 takes the same blocks, with the same results, as the
+    run from 0 to 1/16, across t = 0 included."""
+    n, eps2, eta, dt_max = 256, 1e-3, 0.02, 2.0 ** -6
+    m, x, v = W.plummer(n, 5)
+    prec = sp2.SP2_MIXED if mixed else sp2.SP2_FP64
+    xa, va, ta, sa = _gpu_run(sp2, prec, m, x, v, eps2, 2.0 ** -4, eta, 0.01, dt_max)
+    xb, vb, tb, sb = _gpu_run(sp2, prec, m, x, v, eps2, 2.0 ** -5, eta, 0.01, dt_max, t0=-(2.0 ** -5))
+    assert np.all(ta == 2.0 ** -4) and np.all(tb == 2.0 ** -5)
+    assert sa["block_steps"] == sb["block_steps"] and sa["active_sum"] == sb["active_sum"]
+    assert sb["t"] == 2.0 ** -5
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
