@@ -21,6 +21,10 @@ constexpr int kThreads = 256;
 constexpr double kBlockDtMin = 1.0 / (1ll << 50);  // smallest block step (2^-50)
 
 inline unsigned grid_for(int64_t n) { return static_cast<unsigned>((n + kThreads - 1) / kThreads); }
+// FP64-heavy per-particle kernels over a few hundred active particles: one
+// warp per CTA spreads them over the SMs (an SM retires 2 FP64 FMAs a clock)
+constexpr int kWarpCta = 32;
+inline unsigned grid_for_warps(int64_t n) { return static_cast<unsigned>((n + kWarpCta - 1) / kWarpCta); }
 
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
@@ -228,7 +232,15 @@ __device__ __forceinline__ double norm3(const double *p) { return sqrt(p[0] * p[
 __device__ __forceinline__ double quantise_dt(double want, double cap, double t1) {
     double d = cap;
     while (d > want && d > kBlockDtMin) d *= 0.5;
-    while (d > kBlockDtMin && fmod(t1, d) != 0.0) d *= 0.5;
+    // d divides t1 exactly iff fmod(t1, d) == 0.  A multiple k d gives the
+    // quotient k exactly (the division is correctly rounded and k, or its
+    // rounding above 2^53, is an integer), so a fractional quotient rules d
+    // out without the slow fmod; fmod confirms the candidate that survives.
+    while (d > kBlockDtMin) {
+        const double q = t1 / d;
+        if (q == trunc(q) && fmod(t1, d) == 0.0) break;
+        d *= 0.5;
+    }
     return d;
 }
 
@@ -486,15 +498,17 @@ cudaError_t launch_predict(int order, int mixed, const JStore &js, int64_t n, do
         else predict_ds_kernel<4><<<g, kThreads, 0, s>>>(js.dsc, n, th, tl, rec, bd);
         return cudaGetLastError();
     }
+    // the FP64 predictor is FP64-bound: 64-thread CTAs spread it over the SMs
+    const unsigned g64 = static_cast<unsigned>((n + 63) / 64);
     if (order == 6) {
-        if (mixed) predict_kernel<6, true><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
-        else predict_kernel<6, false><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
+        if (mixed) predict_kernel<6, true><<<g64, 64, 0, s>>>(js, n, t, rec, bd);
+        else predict_kernel<6, false><<<g64, 64, 0, s>>>(js, n, t, rec, bd);
     } else if (order == 2) {
-        if (mixed) predict_kernel<2, true><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
-        else predict_kernel<2, false><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
+        if (mixed) predict_kernel<2, true><<<g64, 64, 0, s>>>(js, n, t, rec, bd);
+        else predict_kernel<2, false><<<g64, 64, 0, s>>>(js, n, t, rec, bd);
     } else {
-        if (mixed) predict_kernel<4, true><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
-        else predict_kernel<4, false><<<g, kThreads, 0, s>>>(js, n, t, rec, bd);
+        if (mixed) predict_kernel<4, true><<<g64, 64, 0, s>>>(js, n, t, rec, bd);
+        else predict_kernel<4, false><<<g64, 64, 0, s>>>(js, n, t, rec, bd);
     }
     return cudaGetLastError();
 }
@@ -539,7 +553,7 @@ cudaError_t launch_block_correct_dev(const JStore &js, double *dt, const int32_t
                                      BlockDev *bd, const double *a1, const double *j1, double eta, double dt_max,
                                      cudaStream_t s) {
     if (n_max <= 0) return cudaSuccess;
-    block_correct_dev_kernel<<<grid_for(n_max), kThreads, 0, s>>>(js, dt, active, bd, a1, j1, eta, dt_max);
+    block_correct_dev_kernel<<<grid_for_warps(n_max), kWarpCta, 0, s>>>(js, dt, active, bd, a1, j1, eta, dt_max);
     return cudaGetLastError();
 }
 
