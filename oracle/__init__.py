@@ -17,12 +17,17 @@ Contents
 ``hermite4_shared``   shared-step 4th-order Hermite integrator (test driver)
 ``hermite4_block``    block time-step 4th-order Hermite integrator with
                       Aarseth's criterion (Sec. 3.7; test driver)
+``hermite6_shared``   shared-step 6th-order Hermite integrator (Nitadori &
+                      Makino 2008; crackle in the predictor; test driver)
+``hermite6_block``    block time-step 6th-order Hermite integrator with the
+                      averaged 4th/6th-order criterion (Sec. 3.7; test driver)
 ``adjoint``           float64 torch restatement for gradient checks (adjoint.py)
 
 Parity status: every output is pinned by the ``-m "not gpu"`` tests
 (brute force in 50-digit decimal arithmetic, two-body Kepler closed form,
 Newton's third law, pair-sum symmetry, finite differences along the predictor,
-invariances, Hermite energy conservation; neighbour lists against scipy's
+invariances, Hermite energy conservation, 6th-order Hermite exactness on a
+quintic and 6th-order convergence on a Kepler orbit; neighbour lists against scipy's
 pairwise distances on an exact integer grid, symmetry, strictness, overflow).
 """
 from __future__ import annotations
@@ -284,6 +289,129 @@ def hermite4_block(m, x, v, eps2: float, t_end: float, eta: float, eta_s: float,
         for k, i in enumerate(act):
             den = J[k] * A3[k] + A2[k] * A2[k]
             want = math.sqrt(eta * (A[k] * A2[k] + J[k] * J[k]) / den) if den > 0 else dt_max
+            dt[i] = _quantise(want, min(2.0 * float(h[k, 0]), dt_max), t1)
+        steps += 1
+        active_sum += len(act)
+    return x, v, t, {"block_steps": steps, "active_sum": active_sum, "dt": dt}
+
+
+def _h6_predict(h, x, v, a, j, s, c):
+    """Taylor prediction over h (per-row column vector) of the 6th-order
+    scheme: x to h^5 (crackle c), v to h^4, a to h^3."""
+    h2, h3 = h * h, h * h * h
+    xp = x + v * h + a * (h2 / 2) + j * (h3 / 6) + s * (h2 * h2 / 24) + c * (h3 * h2 / 120)
+    vp = v + a * h + j * (h2 / 2) + s * (h3 / 6) + c * (h2 * h2 / 24)
+    ap = a + j * h + s * (h2 / 2) + c * (h3 / 6)
+    return xp, vp, ap
+
+
+def _h6_correct(h, x0, v0, a0, j0, s0, a1, j1, s1):
+    """6th-order Hermite corrector (Nitadori & Makino 2008): the quintic
+    Hermite interpolant of the acceleration through (a, j, s) at both ends,
+    integrated once for v and (with v, a, j in place of a, j, s) for x:
+        v1 = v0 + h/2 (a0 + a1) - h^2/10 (j1 - j0) + h^3/120 (s0 + s1)
+        x1 = x0 + h/2 (v0 + v1) - h^2/10 (a1 - a0) + h^3/120 (j0 + j1).
+    The same interpolant's 3rd, 4th and 5th derivatives at the end of the step
+    (crackle, pop and its derivative), written out from the three matching
+    conditions at t1:
+        c1 h^3 = 60 (a1 - a0) - 24 h j0 - 36 h j1 - 3 h^2 s0 + 9 h^2 s1
+        p1 h^4 = 360 (a1 - a0) - 168 h j0 - 192 h j1 - 24 h^2 s0 + 36 h^2 s1
+        q  h^5 = 720 (a1 - a0) - 360 h (j0 + j1) - 60 h^2 (s0 - s1).
+    Returns (x1, v1, c1, p1, q)."""
+    h2 = h * h
+    h3 = h2 * h
+    v1 = v0 + (a0 + a1) * (h / 2) - (j1 - j0) * (h2 / 10) + (s0 + s1) * (h3 / 120)
+    x1 = x0 + (v0 + v1) * (h / 2) - (a1 - a0) * (h2 / 10) + (j0 + j1) * (h3 / 120)
+    da = a1 - a0
+    c1 = (60.0 * da - h * (24.0 * j0 + 36.0 * j1) + h2 * (9.0 * s1 - 3.0 * s0)) / h3
+    p1 = (360.0 * da - h * (168.0 * j0 + 192.0 * j1) + h2 * (36.0 * s1 - 24.0 * s0)) / (h3 * h)
+    q = (720.0 * da - 360.0 * h * (j0 + j1) - 60.0 * h2 * (s0 - s1)) / (h3 * h2)
+    return x1, v1, c1, p1, q
+
+
+def hermite6_shared(m, x, v, eps2: float, dt: float, n_steps: int):
+    """Shared-time-step 6th-order Hermite integration (Nitadori & Makino 2008).
+
+    Per step: predict x, v, a with _h6_predict (crackle from the previous
+    step's interpolation, zero on the first step), evaluate acc, jerk and snap
+    at the predicted state (order-6 direct sum), correct with _h6_correct.
+    Returns the final (x, v)."""
+    n = len(m)
+    ids = np.arange(n, dtype=np.int32)
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    z = np.zeros((n, 3))
+    f = forces(ids, x, v, ids, m, x, v, eps2, 6, ai=z, aj=z)
+    a, j = f["acc"], f["jerk"]
+    # snap needs the sources' accelerations: one more pass with a known
+    f = forces(ids, x, v, ids, m, x, v, eps2, 6, ai=a, aj=a)
+    a, j, s = f["acc"], f["jerk"], f["snap"]
+    c = np.zeros((n, 3))
+    h = np.full((n, 1), dt)
+    for _ in range(n_steps):
+        xp, vp, ap = _h6_predict(h, x, v, a, j, s, c)
+        f = forces(ids, xp, vp, ids, m, xp, vp, eps2, 6, ai=ap, aj=ap)
+        x, v, c, _, _ = _h6_correct(h, x, v, a, j, s, f["acc"], f["jerk"], f["snap"])
+        a, j, s = f["acc"], f["jerk"], f["snap"]
+    return x, v
+
+
+def _h6_step_want(eta4, eta6, a1, j1, s1, c1, p1, q):
+    """Next step of a particle from the end-of-step derivatives: the average
+    of Aarseth's 4th-order criterion and the 6th-order generalisation
+    (Nitadori & Makino 2008),
+        dt4 = sqrt(eta4 (|a||s| + |j|^2) / (|j||c| + |s|^2))
+        dt6 = eta6 ((|a||s| + |j|^2) / (|c||q| + |p|^2))^(1/6)."""
+    A, J, S = np.linalg.norm(a1), np.linalg.norm(j1), np.linalg.norm(s1)
+    C, P, Q = np.linalg.norm(c1), np.linalg.norm(p1), np.linalg.norm(q)
+    num = A * S + J * J
+    d4 = J * C + S * S
+    d6 = C * Q + P * P
+    if not (d4 > 0.0 and d6 > 0.0):
+        return math.inf
+    return 0.5 * (math.sqrt(eta4 * num / d4) + eta6 * (num / d6) ** (1.0 / 6.0))
+
+
+def hermite6_block(m, x, v, eps2: float, t_end: float, eta4: float, eta6: float, eta_s: float,
+                   dt_max: float):
+    """Block time-step 6th-order Hermite integration (Sec. 3.7 runs this
+    scheme with the averaged criterion, eta4 = 0.01 and eta6 = 0.1).
+
+    Start at t = 0 with a, jerk, snap from the direct sum, crackle 0 and steps
+    eta_s |a|/|j|.  Each block: t1 = min(t_i + dt_i); every particle is
+    predicted to t1 (_h6_predict with its own crackle); the active ones get
+    a1, j1, s1 on the predicted state, _h6_correct, a new crackle, and the
+    next step from _h6_step_want quantised by _quantise with cap
+    min(2h, dt_max).  Returns (x, v, t, stats)."""
+    n = len(m)
+    ids = np.arange(n, dtype=np.int32)
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    z = np.zeros((n, 3))
+    f = forces(ids, x, v, ids, m, x, v, eps2, 6, ai=z, aj=z)
+    f = forces(ids, x, v, ids, m, x, v, eps2, 6, ai=f["acc"], aj=f["acc"])
+    a, j, s = f["acc"].copy(), f["jerk"].copy(), f["snap"].copy()
+    c = np.zeros((n, 3))
+    t = np.zeros(n)
+    dt = np.empty(n)
+    for i in range(n):
+        an, jn = np.linalg.norm(a[i]), np.linalg.norm(j[i])
+        dt[i] = _quantise(eta_s * an / jn if jn > 0 else dt_max, dt_max, 0.0)
+    steps, active_sum = 0, 0
+    while True:
+        t1 = float(np.min(t + dt))
+        if t1 > t_end:
+            break
+        act = np.flatnonzero(t + dt == t1)
+        hh = (t1 - t)[:, None]
+        xp, vp, ap = _h6_predict(hh, x, v, a, j, s, c)
+        f = forces(ids[act], xp[act], vp[act], ids, m, xp, vp, eps2, 6, ai=ap[act], aj=ap)
+        a1, j1, s1 = f["acc"], f["jerk"], f["snap"]
+        h = hh[act]
+        x1, v1, c1, p1, q = _h6_correct(h, x[act], v[act], a[act], j[act], s[act], a1, j1, s1)
+        x[act], v[act], a[act], j[act], s[act], c[act], t[act] = x1, v1, a1, j1, s1, c1, t1
+        for k, i in enumerate(act):
+            want = _h6_step_want(eta4, eta6, a1[k], j1[k], s1[k], c1[k], p1[k], q[k])
             dt[i] = _quantise(want, min(2.0 * float(h[k, 0]), dt_max), t1)
         steps += 1
         active_sum += len(act)
