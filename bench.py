@@ -56,8 +56,8 @@ def parse():
     p.add_argument("--n", type=int, default=131072)
     p.add_argument("--n-active", type=int, default=131072)
     p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint / lists lines")
-    p.add_argument("--extras", default="c1,sweep,h6,batched,adjoint,nb,h2,blk",
-                   help="comma-separated secondary sections to run: sweep, h6, batched, adjoint")
+    p.add_argument("--extras", default="c1,sweep,h6,batched,adjoint,nb,h2,blk,blk6",
+                   help="comma-separated secondary sections: c1, sweep, h6, batched, adjoint, nb, h2, blk, blk6")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
@@ -435,6 +435,8 @@ def extras(sp2, w, n, eps2, dev, stream, sections):
             res["h2"] = bench_h2(sp2, dev, stream)
         if "blk" in sections:
             res["blk"] = bench_blk(sp2, dev, stream)
+        if "blk6" in sections:
+            res["blk6"] = bench_blk6(sp2, dev, stream)
     return res
 
 
@@ -676,6 +678,57 @@ def bench_blk(sp2, dev, stream, n=16384, t_end=0.25):
         w0 = time.perf_counter()
         c.block_init(0.0, 0.01, 1.0 / 16)
         st = c.block_run(t_end, 0.01, 1.0 / 16)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        xs, vs = np.empty((n, 3)), np.empty((n, 3))
+        c.get_j(0, n, x=xs, v=vs)
+        c.close()
+        rows.append({"precision": name, "n": n, "t_end": t_end, "wall_s": wall, "block_steps": st["block_steps"],
+                     "mean_active": st["active_sum"] / max(st["block_steps"], 1),
+                     "interactions_per_s": st["active_sum"] * n / wall,
+                     "energy_error": abs(energy(xs, vs) / e0 - 1.0)})
+    return rows
+
+
+def bench_blk6(sp2, dev, stream, n=16384, t_end=0.125):
+    """6th-order block time-steps with the averaged criterion (eta4 = 0.01,
+    eta6 = 0.1, steps <= 1/16; the scheme and parameters of Sec. 3.7) on a
+    Plummer sphere, eps = 1e-3, mixed and FP64: wall time, blocks, mean
+    N_active and the relative energy error at t_end (energies from an FP64
+    context of the library)."""
+    import time
+    import torch
+    eps2 = 1e-6
+    m, x, v = W.plummer(n, 21)
+    ids = np.arange(n, dtype=np.int32)
+    z = np.zeros((n, 3))
+
+    def energy(xx, vv):
+        c = sp2.Context(order=4, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0,
+                        cuda_stream=stream.cuda_stream)
+        c.set_j(0, ids, m, xx, vv, z, z, None, np.zeros(n))
+        c.predict(0.0)
+        pot = np.empty(n)
+        c.compute(ids, pot=pot)
+        c.close()
+        return 0.5 * float(np.sum(m * np.sum(vv * vv, axis=1))) + 0.5 * float(np.sum(m * pot))
+
+    e0 = energy(x, v)
+    rows = []
+    for prec, name in ((sp2.SP2_MIXED, "mixed"), (sp2.SP2_FP64, "fp64")):
+        c = sp2.Context(order=6, precision=prec, n_max=n, eps2=eps2, with_nn=0, cuda_stream=stream.cuda_stream)
+        c.set_j(0, ids, m, x, v, z, z, z, np.zeros(n))
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        c.block_init(0.0, 0.01, 1.0 / 16)
+        try:
+            st = c.block_run_h6(t_end, 0.01, 0.1, 1.0 / 16)
+        except sp2.SP2Error as e:  # step underflow (the collapse Sec. 3.7 warns of for DS forces)
+            torch.cuda.synchronize()
+            rows.append({"precision": name, "n": n, "t_end": t_end, "wall_s": time.perf_counter() - w0,
+                         "stopped": str(e)})
+            c.close()
+            continue
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
         xs, vs = np.empty((n, 3)), np.empty((n, 3))

@@ -244,11 +244,13 @@ sp2_status sp2_get_j(sp2_ctx *ctx, int64_t first, int64_t n, double *x, double *
 
 /* Block time-steps (Sec. 3.7: individual power-of-two time-steps; the paper
  * leaves the integrator to the host, here it runs on the device around the
- * force pass).  Order-4 contexts only.
+ * force pass).  Order-4 contexts (sp2_block_run) and order-6 contexts
+ * (sp2_block_run_h6).
  * sp2_block_init: the loaded particles (x, v and m, with t = t0 for all) get
- *   their acceleration and jerk at t0 from one full pass and initial steps
- *   eta_s |a| / |j|, each the largest power of two not above that, dt_max at
- *   most, dividing t0.
+ *   their acceleration and jerk (order 6: and snap, from a second pass that
+ *   uses the first pass's accelerations; crackles zero) at t0 from a full
+ *   pass and initial steps eta_s |a| / |j|, each the largest power of two not
+ *   above that, dt_max at most, dividing t0.
  * sp2_block_run: repeat until the next block time exceeds t_end: the block
  *   time t1 = min_i(t_i + dt_i), the active set {i : t_i + dt_i = t1}, the
  *   prediction of all particles to t1, the force pass on the active set, and
@@ -266,8 +268,27 @@ sp2_status sp2_get_j(sp2_ctx *ctx, int64_t first, int64_t n, double *x, double *
  *   source split) from the active count on the device.  Runs on the context's
  *   stream and returns after synchronising it; a stream that cannot be
  *   captured gets plain launches throughout.
- * Errors: SP2_ERR_UNSUPPORTED (order), SP2_ERR_STATE (nothing loaded, or
- * block_run without block_init after the last sp2_set_j), SP2_ERR_ARG. */
+ * sp2_block_run_h6: the same loop with the 6th-order Hermite scheme
+ *   (Nitadori & Makino 2008; Sec. 3.7 runs it): the predictor carries each
+ *   particle's crackle from its last correction (x to dt^5, v to dt^4, a to
+ *   dt^3; FP64 arithmetic in both precisions), the pass gives acc, jerk and
+ *   snap, and the corrector
+ *     v1 = v0 + h/2 (a0 + a1) - h^2/10 (j1 - j0) + h^3/120 (s0 + s1)
+ *     x1 = x0 + h/2 (v0 + v1) - h^2/10 (a1 - a0) + h^3/120 (j0 + j1)
+ *   is followed by the crackle, pop and 5th derivative at t1 of the quintic
+ *   interpolant and the next step: the mean of Aarseth's criterion
+ *   sqrt(eta4 (|a||s| + |j|^2) / (|j||c| + |s|^2)) and its 6th-order
+ *   generalisation eta6 ((|a||s| + |j|^2) / (|c||q| + |p|^2))^(1/6),
+ *   quantised as above (Sec. 3.7 uses eta4 = 0.01, eta6 = 0.1).
+ * A new step at the 2^-50 floor stops the run after that block with
+ *   SP2_ERR_RANGE (the particles stay at their last times, *stats is filled):
+ *   the criterion has collapsed.  Sec. 3.7 warns of this for the 6th-order
+ *   criterion on double-single forces, whose noisy jerk and snap enter the
+ *   interpolated higher derivatives amplified by h^-3 to h^-5.
+ * Errors: SP2_ERR_UNSUPPORTED (order; sp2_block_run on an order-6 context or
+ * sp2_block_run_h6 on an order-4 one), SP2_ERR_STATE (nothing loaded, or
+ * block_run without block_init after the last sp2_set_j), SP2_ERR_ARG,
+ * SP2_ERR_RANGE (step underflow). */
 typedef struct {
     int64_t block_steps;   /* force passes taken                          */
     int64_t active_sum;    /* sum of N_active over the passes             */
@@ -278,6 +299,8 @@ typedef struct {
 sp2_status sp2_block_init(sp2_ctx *ctx, double t0, double eta_s, double dt_max);
 sp2_status sp2_block_run(sp2_ctx *ctx, double t_end, double eta, double dt_max,
                          sp2_block_stats *stats);
+sp2_status sp2_block_run_h6(sp2_ctx *ctx, double t_end, double eta4, double eta6, double dt_max,
+                            sp2_block_stats *stats);
 
 /* One shared time-step of the 4th-order Hermite scheme (Makino & Aarseth 1992)
  * on device arrays, in place: predict (x, v) with (a, jerk), evaluate acc and

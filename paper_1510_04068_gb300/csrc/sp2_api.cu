@@ -74,6 +74,8 @@ struct sp2_ctx {
     size_t sinkrec_cap = 0, noslot_cap = 0;
     double *blk_dt = nullptr;               // block time-steps: per-slot step
     BlockDev *blk_dev = nullptr;            // block time-steps: device-driven run state
+    double *blk_cr = nullptr, *blk_s1 = nullptr;  // 6th-order block steps: crackles, new snaps
+    size_t blk_cr_cap = 0, blk_s1_cap = 0;
     int32_t *blk_active = nullptr;          // block time-steps: active slots
     size_t blk_dt_cap = 0, blk_active_cap = 0;
     bool blk_ready = false;                 // sp2_block_init has run since the last set_j
@@ -305,8 +307,8 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     const int fused = (!n_i_dev && allow_fused && kind == K_FORCE && mixed && c->js.dsc && n_iblk == 1) ? 1 : 0;
     if (!fused && allow_fused && !n_i_dev) SP2_CKS(materialize(c));
     const int devn = n_i_dev ? 1 : 0;
-    if (devn && (kind != K_FORCE || order != 4 || nn || nb || L.i_per_thread != 1))
-        return fail(c, SP2_ERR_UNSUPPORTED, "device-count passes are order-4 forces without neighbours");
+    if (devn && (kind != K_FORCE || (order != 4 && order != 6) || nn || nb || L.i_per_thread != 1))
+        return fail(c, SP2_ERR_UNSUPPORTED, "device-count passes are order-4/6 forces without neighbours");
     KernelKey key{kind, order, mixed, nn, L.i_per_thread, fused, nb, devn};
     int64_t split = std::max<int64_t>(1, std::min<int64_t>(L.split_j, ceil_div(n_j, tile)));
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
@@ -1111,7 +1113,8 @@ sp2_status sp2_get_j(sp2_ctx *c, int64_t first, int64_t n, double *x, double *v,
 
 sp2_status sp2_block_init(sp2_ctx *c, double t0, double eta_s, double dt_max) {
     SP2_CKS(usable(c));
-    if (c->cfg.order != 4) return fail(c, SP2_ERR_UNSUPPORTED, "block time-steps need an order-4 context");
+    if (c->cfg.order != 4 && c->cfg.order != 6)
+        return fail(c, SP2_ERR_UNSUPPORTED, "block time-steps need an order-4 or order-6 context");
     if (c->n_loaded == 0) return fail(c, SP2_ERR_STATE, "no j-particles loaded");
     if (c->capturing) return fail(c, SP2_ERR_STATE, "cannot start block steps during graph capture");
     if (!std::isfinite(t0) || !(eta_s > 0.0) || !(dt_max > 0.0) || !std::isfinite(dt_max))
@@ -1119,31 +1122,57 @@ sp2_status sp2_block_init(sp2_ctx *c, double t0, double eta_s, double dt_max) {
     const int64_t n = c->n_loaded;
     SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->blk_dt), &c->blk_dt_cap, n * sizeof(double), "block-step"));
     SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->blk_active), &c->blk_active_cap, n * sizeof(int32_t), "block-step"));
-    // a and jerk of every particle at t0 (the stored times are taken to be t0)
-    SP2_CKS(sp2_predict(c, t0));
+    const int order = c->cfg.order;
+    // a and jerk (and snap) of every particle at t0 (the stored times are
+    // taken to be t0); the snap needs the sources' accelerations, so the
+    // 6th-order start takes a second pass with the accelerations of the first
     PassOut o;
     o.acc = c->js.a;  // the pass reads the predicted records, not the store
     o.jerk = c->js.jk;
-    SP2_CKS(materialize(c));
-    SP2_CKS(run_pass(c, K_FORCE, 4, c->cfg.precision == SP2_MIXED, 0, c->rec, c->rb, n, c->iota, n, 0, n, o, nullptr,
-                     ST_FORCE));
+    o.snap = (order == 6) ? c->js.sn : nullptr;
+    for (int pass = 0; pass < (order == 6 ? 2 : 1); ++pass) {
+        if (pass > 0) {
+            if (c->js.dsc) SP2_CK(c, launch_dscache(order, c->js, 0, n, c->stream));
+            c->rec_valid = false;
+        }
+        SP2_CKS(sp2_predict(c, t0));
+        SP2_CKS(materialize(c));
+        SP2_CKS(run_pass(c, K_FORCE, order, c->cfg.precision == SP2_MIXED, 0, c->rec, c->rb, n, c->iota, n, 0, n, o,
+                         nullptr, ST_FORCE));
+    }
     SP2_CK(c, launch_block_init(c->js, c->blk_dt, n, eta_s, dt_max, t0, c->stream));
-    if (c->js.dsc) SP2_CK(c, launch_dscache(c->cfg.order, c->js, 0, n, c->stream));
+    if (c->js.dsc) SP2_CK(c, launch_dscache(order, c->js, 0, n, c->stream));
     c->launches += 2;
+    if (order == 6) {  // crackles start at zero
+        SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->blk_cr), &c->blk_cr_cap, 3 * n * sizeof(double), "block-step"));
+        SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->blk_s1), &c->blk_s1_cap, 3 * n * sizeof(double), "block-step"));
+        SP2_CK(c, cudaMemsetAsync(c->blk_cr, 0, 3 * n * sizeof(double), c->stream));
+    }
     c->rec_valid = false;
     c->blk_ready = true;
     SP2_CK(c, cudaStreamSynchronize(c->stream));
     return SP2_OK;
 }
 
-sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp2_block_stats *st) {
+// eta: Aarseth's parameter (4th order) or eta4 of the averaged criterion (6th)
+static sp2_status block_run_impl(sp2_ctx *c, double t_end, double eta, double eta6, double dt_max,
+                                 sp2_block_stats *st) {
     SP2_CKS(usable(c));
     if (!c->blk_ready) return fail(c, SP2_ERR_STATE, "call sp2_block_init first");
     if (c->capturing) return fail(c, SP2_ERR_STATE, "cannot run block steps during graph capture");
     if (!std::isfinite(t_end) || !(eta > 0.0) || !(dt_max > 0.0)) return fail(c, SP2_ERR_ARG, "bad t_end, eta or dt_max");
     const int64_t n = c->n_loaded;
     const int mixed = c->cfg.precision == SP2_MIXED;
-    double *a1 = c->tmp, *j1 = c->tmp + 3 * c->cfg.n_max;
+    const int order = c->cfg.order;
+    double *a1 = c->tmp, *j1 = c->tmp + 3 * c->cfg.n_max, *s1 = c->blk_s1;
+    // 6th order: the predictor adds the crackles (FP64 arithmetic, also for
+    // mixed records: the double-single cache holds none); the corrector
+    // updates them and keeps the cache in step
+    JStore jp = c->js, jc = c->js;
+    if (order == 6) {
+        jp.cr = jc.cr = c->blk_cr;
+        jp.dsc = nullptr;
+    }
     if (!c->blk_dev) {
         c->blk_dev = static_cast<BlockDev *>(dalloc(c, sizeof(BlockDev)));
         if (!c->blk_dev) return fail(c, SP2_ERR_NOMEM, "cannot allocate the block-step state");
@@ -1164,9 +1193,10 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
     L.j_lanes = 1;
     L.j_tile = 256;
     L.split_j = static_cast<int>(kFusedReduceMaxValues / L.threads);
-    while (L.split_j > 1 && static_cast<double>(n) * 8.0 * 8.0 * L.split_j > 256.0 * (1 << 20)) L.split_j /= 2;
+    const double fields = (order == 6) ? 10.0 : 7.0;
+    while (L.split_j > 1 && static_cast<double>(n) * fields * 8.0 * L.split_j > 256.0 * (1 << 20)) L.split_j /= 2;
     {
-        KernelKey key{K_FORCE, 4, mixed, 0, 1, 0, 0, 1};
+        KernelKey key{K_FORCE, order, mixed, 0, 1, 0, 0, 1};
         int per_sm = 0;
         SP2_CK(c, force_kernel_occupancy(key, L.threads, L.j_tile, &per_sm));
         if (per_sm <= 0) return fail(c, SP2_ERR_UNSUPPORTED, "block-step pass does not fit on an SM");
@@ -1175,6 +1205,7 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
     PassOut o;
     o.acc = a1;
     o.jerk = j1;
+    o.snap = (order == 6) ? s1 : nullptr;
     // Blocks are queued in batches; a block past t_end sets the stop flag on
     // the device and every later kernel of the batch does nothing.  The first
     // batch is launched directly (it sizes the pass buffers); the rest replay
@@ -1186,13 +1217,17 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
             SP2_CK(c, launch_block_begin(c->blk_dev, c->js.t, c->blk_dt, n, t_end, c->blk_active, c->stream));
             ev_end(c, ST_OTHER);
             ev_begin(c, ST_PREDICT);
-            SP2_CK(c, launch_predict(4, mixed, c->js, n, 0.0, c->rec, c->stream, c->blk_dev));
+            SP2_CK(c, launch_predict(order, mixed, jp, n, 0.0, c->rec, c->stream, c->blk_dev));
             ev_end(c, ST_PREDICT);
-            SP2_CKS(run_pass(c, K_FORCE, 4, mixed, 0, c->rec, c->rb, n, c->blk_active, n, 0, n, o, &L, ST_FORCE,
+            SP2_CKS(run_pass(c, K_FORCE, order, mixed, 0, c->rec, c->rb, n, c->blk_active, n, 0, n, o, &L, ST_FORCE,
                              nullptr, false, &c->blk_dev->count));
             ev_begin(c, ST_OTHER);
-            SP2_CK(c, launch_block_correct_dev(c->js, c->blk_dt, c->blk_active, n, c->blk_dev, a1, j1, eta, dt_max,
-                                               c->stream));
+            if (order == 6)
+                SP2_CK(c, launch_block_correct6_dev(jc, c->blk_dt, c->blk_active, n, c->blk_dev, a1, j1, s1, eta,
+                                                    eta6, dt_max, c->stream));
+            else
+                SP2_CK(c, launch_block_correct_dev(jc, c->blk_dt, c->blk_active, n, c->blk_dev, a1, j1, eta, dt_max,
+                                                   c->stream));
             ev_end(c, ST_OTHER);
             c->launches += 5;  // run_pass counts the force kernel
         }
@@ -1249,7 +1284,23 @@ sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp
         st->min_active = h.steps ? h.min_active : 0;
         st->t = h.t_last;
     }
+    if (h.underflow)
+        return fail(c, SP2_ERR_RANGE, "block time-step underflow (2^-50) at t = %.17g: the step criterion collapsed",
+                    h.t_last);
     return SP2_OK;
+}
+
+sp2_status sp2_block_run(sp2_ctx *c, double t_end, double eta, double dt_max, sp2_block_stats *st) {
+    SP2_CKS(usable(c));
+    if (c->cfg.order != 4) return fail(c, SP2_ERR_UNSUPPORTED, "sp2_block_run takes order-4 contexts (order 6: sp2_block_run_h6)");
+    return block_run_impl(c, t_end, eta, 0.0, dt_max, st);
+}
+
+sp2_status sp2_block_run_h6(sp2_ctx *c, double t_end, double eta4, double eta6, double dt_max, sp2_block_stats *st) {
+    SP2_CKS(usable(c));
+    if (c->cfg.order != 6) return fail(c, SP2_ERR_UNSUPPORTED, "sp2_block_run_h6 takes order-6 contexts");
+    if (!(eta6 > 0.0)) return fail(c, SP2_ERR_ARG, "bad eta6");
+    return block_run_impl(c, t_end, eta4, eta6, dt_max, st);
 }
 
 sp2_status sp2_hermite4_step(sp2_ctx *c, int64_t n, double dt, const double *m, double *x, double *v, double *a,

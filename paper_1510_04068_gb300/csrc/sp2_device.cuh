@@ -1713,14 +1713,18 @@ inline cudaError_t occupancy_pass(int threads, size_t tile, int *blocks) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pass_kernel<P, IPT, FUSED, DEVN>, threads, smem);
 }
 
-// The device-count pass (block time-steps) exists for the order-4 force
-// policies without nearest neighbours, one sink per thread.
+// The device-count pass (block time-steps) exists for the order-4 and
+// order-6 force policies without nearest neighbours, one sink per thread.
 template <class P>
 struct takes_device_count { static constexpr bool value = false; };
 template <>
 struct takes_device_count<MixedPairForce<4, false>> { static constexpr bool value = true; };
 template <>
 struct takes_device_count<Fp64Force<4, false>> { static constexpr bool value = true; };
+template <>
+struct takes_device_count<MixedPairForce<6, false>> { static constexpr bool value = true; };
+template <>
+struct takes_device_count<Fp64Force<6, false>> { static constexpr bool value = true; };
 
 template <class P, bool FUSED>
 inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,

@@ -21,6 +21,9 @@ struct JStore {
     //   {xh yh zh m}{xl yl zl th}{vxh vyh vzh tl}{vxl vyl vzl id}
     //   {axh ayh azh 0}{axl ayl azl 0}{jx jy jz 0}[{sx sy sz 0}]   (float4 words)
     float4 *dsc;
+    // 6th-order block time-steps only: per-particle crackle (n x 3) from the
+    // last correction, added to the predictor when set (null otherwise)
+    double *cr;
 };
 __host__ __device__ constexpr int dscache_words(int order) { return order == 6 ? 8 : 7; }
 
@@ -135,7 +138,7 @@ struct KernelKey {
     int ipt;    // 1 / 2 / 4
     int fused;  // 1: predict sources in the pass (mixed force only)
     int nb;     // 1: neighbour lists (force kernels with nearest neighbour, ipt 1)
-    int devn;   // 1: sink count read on the device, shape derived from it (order 4, no NN, ipt 1)
+    int devn;   // 1: sink count read on the device, shape derived from it (order 4 or 6, no NN, ipt 1)
 };
 
 // Each kernel translation unit provides these for its (order, precision).
@@ -177,7 +180,8 @@ cudaError_t launch_scatter_j(const JStore &dst, const int32_t *slots, int64_t n,
 struct BlockDev {
     unsigned long long t1bits;  // order-preserving key of the current block time
     unsigned int count;         // active particles of the current block (0: none / stopped)
-    unsigned int stop;          // set once the next block time passes t_end
+    unsigned int stop;          // set once the next block time passes t_end (or on underflow)
+    unsigned int underflow;     // a new step fell to the 2^-50 floor: the run stops there
     unsigned long long steps, active_sum;
     unsigned int max_active, min_active;
     double t_last;              // time of the last block taken
@@ -209,6 +213,11 @@ cudaError_t launch_block_begin(BlockDev *bd, const double *t, const double *dt, 
 cudaError_t launch_block_correct_dev(const JStore &js, double *dt, const int32_t *active, int64_t n_max,
                                      BlockDev *bd, const double *a1, const double *j1, double eta, double dt_max,
                                      cudaStream_t s);
+// 6th-order form: s1 the snaps, js.cr the crackles (updated), the averaged
+// criterion with eta4 and eta6
+cudaError_t launch_block_correct6_dev(const JStore &js, double *dt, const int32_t *active, int64_t n_max,
+                                      BlockDev *bd, const double *a1, const double *j1, const double *s1,
+                                      double eta4, double eta6, double dt_max, cudaStream_t s);
 cudaError_t launch_nb_finish(const int32_t *ids, int64_t n_i, int nb_max, const int32_t *count, int32_t *list,
                              cudaStream_t s);
 cudaError_t launch_h4_predict_pack(int mixed, int64_t n, double dt, const double *m,

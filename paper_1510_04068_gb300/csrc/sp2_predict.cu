@@ -164,6 +164,14 @@ __global__ void predict_kernel(JStore js, int64_t n, double t, unsigned char *re
         if (ORDER == 2) {  // leap-frog (GRAPE-5): sources are used where they are
             xp[c] = x;
             vp[c] = 0.0;
+        } else if (ORDER == 6 && js.cr) {
+            // 6th-order block steps: the crackle term too (x to dt^5, v to
+            // dt^4, a to dt^3), Horner form in both precisions
+            const double s = js.sn[q], cr = js.cr[q];
+            const double d5 = dt * (1.0 / 120.0);
+            xp[c] = fma(fma(fma(fma(fma(cr, d5, s * (1.0 / 24.0)), dt, jk * (1.0 / 6.0)), dt, 0.5 * a), dt, v), dt, x);
+            vp[c] = fma(fma(fma(fma(cr, d4, s * (1.0 / 6.0)), dt, 0.5 * jk), dt, a), dt, v);
+            ap[c] = fma(fma(fma(cr, d3, 0.5 * s), dt, jk), dt, a);
         } else if (MIXED && ORDER == 6) {
             const double s = js.sn[q];
             xp[c] = fma(fma(fma(fma(s, d4, jk * (1.0 / 6.0)), dt, 0.5 * a), dt, v), dt, x);
@@ -286,6 +294,15 @@ __device__ __forceinline__ void correct_one(const JStore &js, double *dt, int64_
     if (js.dsc) write_dscache(js, s);
 }
 
+// A step at the 2^-50 floor means the criterion has collapsed (Sec. 3.7 notes
+// that noisy jerk and snap can drive the step to zero): the run stops after
+// this block and the host reports it.
+__device__ __forceinline__ void check_underflow(const double *dt, int64_t s, BlockDev *bd) {
+    if (dt[s] <= kBlockDtMin) {
+        bd->underflow = 1u;
+        bd->stop = 1u;
+    }
+}
 
 // Explicit sinks (sp2_compute_ext): positions / velocities [/ accelerations]
 // given by the caller, packed in the context's record format.
@@ -350,6 +367,72 @@ __global__ void block_correct_dev_kernel(JStore js, double *dt, const int32_t *a
     }
     if (k >= n_act) return;
     correct_one(js, dt, active[k], k, t1, a1, j1, eta, dt_max);
+    check_underflow(dt, active[k], bd);
+}
+
+// 6th-order Hermite corrector (Nitadori & Makino 2008) for slot s, position k
+// of the active list: the quintic Hermite interpolant of the acceleration
+// through (a, j, s) at both ends, integrated once for v and, with (v, a, j),
+// for x; its 3rd to 5th derivatives at t1 (crackle, pop, and the constant
+// fifth derivative q) follow from the three matching conditions at t1:
+//   c1 h^3 = 60 (a1 - a0) - 24 h j0 - 36 h j1 - 3 h^2 s0 + 9 h^2 s1
+//   p1 h^4 = 360 (a1 - a0) - 168 h j0 - 192 h j1 - 24 h^2 s0 + 36 h^2 s1
+//   q  h^5 = 720 (a1 - a0) - 360 h (j0 + j1) - 60 h^2 (s0 - s1).
+// The next step is the mean of Aarseth's criterion (eta4 inside the root)
+// and its 6th-order generalisation (eta6 times the sixth root), quantised
+// like the 4th-order one.
+__device__ __forceinline__ void correct6_one(const JStore &js, double *dt, int64_t s, int64_t k, double t1,
+                                             const double *a1, const double *j1, const double *s1, double eta4,
+                                             double eta6, double dt_max) {
+    const double h = t1 - js.t[s];
+    const double h2 = h * h, h3 = h2 * h;
+    const double ih3 = 1.0 / h3, ih4 = ih3 / h, ih5 = ih4 / h;
+    double an[3], jn[3], sn[3], cn[3], pn[3], qn[3];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = 3 * s + c;
+        const double x0 = js.x[q], v0 = js.v[q], a0 = js.a[q], j0 = js.jk[q], s0 = js.sn[q];
+        const double aa = a1[3 * k + c], jj = j1[3 * k + c], ss = s1[3 * k + c];
+        const double v1 = v0 + (a0 + aa) * (h / 2) - (jj - j0) * (h2 / 10) + (s0 + ss) * (h3 / 120);
+        const double x1 = x0 + (v0 + v1) * (h / 2) - (aa - a0) * (h2 / 10) + (j0 + jj) * (h3 / 120);
+        const double da = aa - a0;
+        cn[c] = (60.0 * da - h * (24.0 * j0 + 36.0 * jj) + h2 * (9.0 * ss - 3.0 * s0)) * ih3;
+        pn[c] = (360.0 * da - h * (168.0 * j0 + 192.0 * jj) + h2 * (36.0 * ss - 24.0 * s0)) * ih4;
+        qn[c] = (720.0 * da - 360.0 * h * (j0 + jj) - 60.0 * h2 * (s0 - ss)) * ih5;
+        an[c] = aa;
+        jn[c] = jj;
+        sn[c] = ss;
+        js.x[q] = x1;
+        js.v[q] = v1;
+        js.a[q] = aa;
+        js.jk[q] = jj;
+        js.sn[q] = ss;
+        js.cr[q] = cn[c];
+    }
+    js.t[s] = t1;
+    const double A = norm3(an), J = norm3(jn), S = norm3(sn), C = norm3(cn), P = norm3(pn), Q = norm3(qn);
+    const double num = A * S + J * J, d4 = J * C + S * S, d6 = C * Q + P * P;
+    const double want = (d4 > 0.0 && d6 > 0.0) ? 0.5 * (sqrt(eta4 * num / d4) + eta6 * pow(num / d6, 1.0 / 6.0))
+                                               : dt_max;
+    dt[s] = quantise_dt(want, fmin(2.0 * h, dt_max), t1);
+    if (js.dsc) write_dscache(js, s);
+}
+
+__global__ void block_correct6_dev_kernel(JStore js, double *dt, const int32_t *active, BlockDev *bd,
+                                          const double *a1, const double *j1, const double *s1, double eta4,
+                                          double eta6, double dt_max) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const unsigned int n_act = bd->count;
+    const double t1 = key_time(bd->t1bits);
+    if (k == 0 && n_act > 0) {
+        bd->steps += 1;
+        bd->active_sum += n_act;
+        bd->max_active = max(bd->max_active, n_act);
+        bd->min_active = min(bd->min_active, n_act);
+        bd->t_last = t1;
+    }
+    if (k >= n_act) return;
+    correct6_one(js, dt, active[k], k, t1, a1, j1, s1, eta4, eta6, dt_max);
+    check_underflow(dt, active[k], bd);
 }
 
 __global__ void iota_kernel(int32_t *dst, int64_t n) {
@@ -554,6 +637,15 @@ cudaError_t launch_block_correct_dev(const JStore &js, double *dt, const int32_t
                                      cudaStream_t s) {
     if (n_max <= 0) return cudaSuccess;
     block_correct_dev_kernel<<<grid_for_warps(n_max), kWarpCta, 0, s>>>(js, dt, active, bd, a1, j1, eta, dt_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_correct6_dev(const JStore &js, double *dt, const int32_t *active, int64_t n_max,
+                                      BlockDev *bd, const double *a1, const double *j1, const double *s1,
+                                      double eta4, double eta6, double dt_max, cudaStream_t s) {
+    if (n_max <= 0) return cudaSuccess;
+    block_correct6_dev_kernel<<<grid_for_warps(n_max), kWarpCta, 0, s>>>(js, dt, active, bd, a1, j1, s1, eta4, eta6,
+                                                                       dt_max);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@ SP2_FP64, SP2_MIXED = 0, 1
 SP2_HOST, SP2_DEVICE = 0, 1
 STATUS = {0: "SP2_OK", -1: "SP2_ERR_ARG", -2: "SP2_ERR_RANGE", -3: "SP2_ERR_NOMEM", -4: "SP2_ERR_CUDA",
           -5: "SP2_ERR_STATE", -6: "SP2_ERR_TIMEOUT", -7: "SP2_ERR_NONFINITE", -8: "SP2_ERR_UNSUPPORTED"}
+(SP2_ERR_ARG, SP2_ERR_RANGE, SP2_ERR_NOMEM, SP2_ERR_CUDA, SP2_ERR_STATE, SP2_ERR_TIMEOUT, SP2_ERR_NONFINITE,
+ SP2_ERR_UNSUPPORTED) = range(-1, -9, -1)
 STAGES = ("predict", "force", "reduce", "batched", "vjp", "other")
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
@@ -64,6 +66,7 @@ _SIGS = [
     ("sp2_get_j", [_P, c_int64, c_int64, _P, _P, _P, _P, _P, c_int], c_int),
     ("sp2_block_init", [_P, c_double, c_double, c_double], c_int),
     ("sp2_block_run", [_P, c_double, c_double, c_double, _P], c_int),
+    ("sp2_block_run_h6", [_P, c_double, c_double, c_double, c_double, _P], c_int),
     ("sp2_batch_plan_create", [_P, c_int64, _P, POINTER(_P)], c_int),
     ("sp2_batch_plan_destroy", [_P], c_int),
     ("sp2_compute_batched", [_P, _P, _P, _P, _P, _P, _P, _P, c_int], c_int),
@@ -237,6 +240,13 @@ def sp2_block_run(ctx, t_end, eta, dt_max):
     return {name: getattr(st, name) for name, _ in st._fields_}
 
 
+def sp2_block_run_h6(ctx, t_end, eta4, eta6, dt_max):
+    """6th-order block time-steps to t_end (averaged criterion); statistics as a dict."""
+    st = sp2_block_stats()
+    _check(load().sp2_block_run_h6(ctx, float(t_end), float(eta4), float(eta6), float(dt_max), byref(st)), ctx)
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
 def sp2_batch_plan_create(ctx, offsets):
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     plan = c_void_p()
@@ -388,6 +398,7 @@ class Context:
     def get_j(self, *a, **k): return sp2_get_j(self.ctx, *a, **k)
     def block_init(self, *a): return sp2_block_init(self.ctx, *a)
     def block_run(self, *a): return sp2_block_run(self.ctx, *a)
+    def block_run_h6(self, *a): return sp2_block_run_h6(self.ctx, *a)
     def batch_plan(self, offsets): return sp2_batch_plan_create(self.ctx, offsets)
     def compute_batched(self, *a, **k): return sp2_compute_batched(self.ctx, *a, **k)
     def forces(self, *a, **k): return sp2_forces(self.ctx, *a, **k)

@@ -81,7 +81,19 @@ def test_block_run_in_stages_and_rules(sp2, oracle_mod):
     c.close()
     c = sp2.Context(order=6, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0)
     c.set_j(0, ids, m, x, v, z, z, z, np.zeros(n))
-    with pytest.raises(sp2.SP2Error):  # order 4 only
+    c.block_init(0.0, 0.01, 2.0 ** -6)
+    with pytest.raises(sp2.SP2Error):  # the 4th-order driver on an order-6 context
+        c.block_run(0.1, 0.01, 2.0 ** -6)
+    c.close()
+    c = sp2.Context(order=4, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0)
+    c.set_j(0, ids, m, x, v, z, z, None, np.zeros(n))
+    c.block_init(0.0, 0.01, 2.0 ** -6)
+    with pytest.raises(sp2.SP2Error):  # the 6th-order driver on an order-4 context
+        c.block_run_h6(0.1, 0.01, 0.1, 2.0 ** -6)
+    c.close()
+    c = sp2.Context(order=2, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0)
+    c.set_j(0, ids, m, x, None, None, None, None, None)
+    with pytest.raises(sp2.SP2Error):  # no block steps for the leap-frog pass
         c.block_init(0.0, 0.01, 2.0 ** -6)
     c.close()
 
@@ -101,3 +113,72 @@ def test_block_run_shift_in_time(sp2, mixed):
     assert sa["block_steps"] == sb["block_steps"] and sa["active_sum"] == sb["active_sum"]
     assert sb["t"] == 2.0 ** -5
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def _gpu_run_h6(sp2, precision, m, x, v, eps2, t_end, eta4, eta6, eta_s, dt_max):
+    n = len(m)
+    c = sp2.Context(order=6, precision=precision, n_max=n, eps2=eps2, with_nn=0)
+    z = np.zeros((n, 3))
+    c.set_j(0, np.arange(n, dtype=np.int32), m, x, v, z, z, z, np.zeros(n))
+    c.block_init(0.0, eta_s, dt_max)
+    st = c.block_run_h6(t_end, eta4, eta6, dt_max)
+    xs, vs, ts = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    c.get_j(0, n, x=xs, v=vs, t=ts)
+    c.close()
+    return xs, vs, ts, st
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_block_run_h6_matches_oracle(sp2, oracle_mod, mixed):
+    """6th-order block steps with the averaged criterion (eta4 = 0.01,
+    eta6 = 0.1, the values Sec. 3.7 uses) against the oracle's integrator."""
+    n, eps2, t_end, dt_max = 256, 1e-3, 2.0 ** -4, 2.0 ** -6
+    m, x, v = W.plummer(n, 12)
+    xo, vo, to, so = oracle_mod.hermite6_block(m, x, v, eps2, t_end, 0.01, 0.1, 0.01, dt_max)
+    xg, vg, tg, sg = _gpu_run_h6(sp2, sp2.SP2_MIXED if mixed else sp2.SP2_FP64, m, x, v, eps2, t_end, 0.01, 0.1,
+                                 0.01, dt_max)
+    assert np.all(tg == t_end) and np.all(to == t_end)
+    dx = np.linalg.norm(xg - xo, axis=1) / np.linalg.norm(xo, axis=1)
+    e0 = oracle_mod.energy(m, x, v, eps2)
+    eg = abs(oracle_mod.energy(m, xg, vg, eps2) / e0 - 1)
+    eo = abs(oracle_mod.energy(m, xo, vo, eps2) / e0 - 1)
+    info = (sg, so["block_steps"], so["active_sum"], float(np.median(dx)), float(dx.max()), eg, eo)
+    assert eo < 1e-10
+    if not mixed:
+        assert abs(sg["block_steps"] - so["block_steps"]) <= 0.05 * so["block_steps"] + 1, info
+        assert abs(sg["active_sum"] - so["active_sum"]) <= 0.05 * so["active_sum"], info
+        assert np.median(dx) < 1e-12 and dx.max() < 1e-8, info
+        assert eg < 1e-10, info
+    else:
+        # double-single forces: the noise of jerk and snap, amplified in the
+        # interpolated crackle, pop and 5th derivative, shortens some steps
+        # (Sec. 3.7 sees fewer active particles per block with DS forces)
+        assert so["block_steps"] * 0.95 <= sg["block_steps"] <= 4 * so["block_steps"], info
+        assert np.median(dx) < 1e-5 and dx.max() < 1e-3, info
+        assert eg < 1e-6, info
+
+
+def test_block_run_h6_fp64_convergence_and_underflow_guard(sp2, oracle_mod):
+    """FP64 6th-order block steps: the energy error falls with the criterion
+    parameters, as in the oracle's pin; a criterion asking for steps below
+    the 2^-50 floor stops the run with SP2_ERR_RANGE after one block."""
+    n, eps2, t_end, dt_max = 256, 1e-3, 2.0 ** -3, 2.0 ** -5
+    m, x, v = W.plummer(n, 8)
+    e0 = oracle_mod.energy(m, x, v, eps2)
+    errs = []
+    for eta4, eta6 in ((0.04, 0.4), (0.01, 0.1)):
+        xg, vg, tg, sg = _gpu_run_h6(sp2, sp2.SP2_FP64, m, x, v, eps2, t_end, eta4, eta6, 0.01, dt_max)
+        assert np.all(tg == t_end)
+        errs.append(abs(oracle_mod.energy(m, xg, vg, eps2) / e0 - 1))
+    assert errs[1] < 1e-10 and errs[1] < errs[0] / 20, errs
+    c = sp2.Context(order=6, precision=sp2.SP2_FP64, n_max=n, eps2=eps2, with_nn=0)
+    z = np.zeros((n, 3))
+    c.set_j(0, np.arange(n, dtype=np.int32), m, x, v, z, z, z, np.zeros(n))
+    c.block_init(0.0, 0.01, dt_max)
+    with pytest.raises(sp2.SP2Error) as ei:
+        c.block_run_h6(t_end, 1e-40, 1e-40, dt_max)
+    assert ei.value.status == sp2.SP2_ERR_RANGE and "underflow" in str(ei.value)
+    ts = np.empty(n)
+    c.get_j(0, n, t=ts)
+    assert 0 < np.count_nonzero(ts > 0) < n  # one block was taken, then the run stopped
+    c.close()
