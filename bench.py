@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the sweep / FP64 / batched / adjoint / lists lines")
     p.add_argument("--extras", default="c1,sweep,h6,batched,adjoint,nb,h2,blk,blk6",
                    help="comma-separated secondary sections: c1, sweep, h6, batched, adjoint, nb, h2, blk, blk6")
+    p.add_argument("--blk-t-end", type=float, default=0.25,
+                   help="end time of the 4th-order block time-step line (blk)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
@@ -365,7 +367,7 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         line["e2e"] = e2e(ctx, w, upd, out, args, stream)
     if not args.no_extras and rank == 0:
-        line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")))
+        line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")), args.blk_t_end)
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -413,7 +415,7 @@ def timed(fn, reps, stream):
     return statistics.median(ts)
 
 
-def extras(sp2, w, n, eps2, dev, stream, sections):
+def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25):
     """N_active sweep (mixed vs FP64), batched systems, adjoint: secondary lines."""
     import torch
     D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
@@ -434,7 +436,7 @@ def extras(sp2, w, n, eps2, dev, stream, sections):
         if "h2" in sections:
             res["h2"] = bench_h2(sp2, dev, stream)
         if "blk" in sections:
-            res["blk"] = bench_blk(sp2, dev, stream)
+            res["blk"] = bench_blk(sp2, dev, stream, t_end=blk_t_end)
         if "blk6" in sections:
             res["blk6"] = bench_blk6(sp2, dev, stream)
     return res
