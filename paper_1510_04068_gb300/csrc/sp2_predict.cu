@@ -240,14 +240,20 @@ __device__ __forceinline__ double norm3(const double *p) { return sqrt(p[0] * p[
 __device__ __forceinline__ double quantise_dt(double want, double cap, double t1) {
     double d = cap;
     while (d > want && d > kBlockDtMin) d *= 0.5;
-    // d divides t1 exactly iff fmod(t1, d) == 0.  A multiple k d gives the
-    // quotient k exactly (the division is correctly rounded and k, or its
-    // rounding above 2^53, is an integer), so a fractional quotient rules d
-    // out without the slow fmod; fmod confirms the candidate that survives.
+    // d = cap 2^-k divides t1 exactly iff fmod(t1, d) == 0.  With r = t1 / cap
+    // (one correctly rounded division), a multiple t1 = m d gives r = m 2^-k
+    // exactly for m < 2^53, so q = r 2^k (an exact scaling) is the integer m;
+    // above 2^53 every double is an integer.  A fractional q therefore rules d
+    // out, and the candidate that survives is confirmed exactly: t1 - q d by
+    // one fused multiply-add (zero iff t1 = q d) below 2^53, fmod above.
+    double q = (t1 / cap) * (cap / d);
     while (d > kBlockDtMin) {
-        const double q = t1 / d;
-        if (q == trunc(q) && fmod(t1, d) == 0.0) break;
+        if (q == trunc(q)) {
+            const bool exact = (fabs(q) < 9007199254740992.0) ? (fma(-q, d, t1) == 0.0) : (fmod(t1, d) == 0.0);
+            if (exact) break;
+        }
         d *= 0.5;
+        q *= 2.0;
     }
     return d;
 }
