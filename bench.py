@@ -692,7 +692,7 @@ def bench_blk(sp2, dev, stream, n=16384, t_end=0.25):
     return rows
 
 
-def bench_blk6(sp2, dev, stream, n=16384, t_end=0.125):
+def bench_blk6(sp2, dev, stream, n=16384, t_end=0.03125):
     """6th-order block time-steps with the averaged criterion (eta4 = 0.01,
     eta6 = 0.1, steps <= 1/16; the scheme and parameters of Sec. 3.7) on a
     Plummer sphere, eps = 1e-3, mixed and FP64: wall time, blocks, mean

@@ -276,8 +276,10 @@ sp2_status sp2_get_j(sp2_ctx *ctx, int64_t first, int64_t n, double *x, double *
  *     v1 = v0 + h/2 (a0 + a1) - h^2/10 (j1 - j0) + h^3/120 (s0 + s1)
  *     x1 = x0 + h/2 (v0 + v1) - h^2/10 (a1 - a0) + h^3/120 (j0 + j1)
  *   is followed by the crackle, pop and 5th derivative at t1 of the quintic
- *   interpolant and the next step: the mean of Aarseth's criterion
- *   sqrt(eta4 (|a||s| + |j|^2) / (|j||c| + |s|^2)) and its 6th-order
+ *   interpolant and the next step: the mean of Aarseth's criterion as the
+ *   4th-order driver evaluates it (a, jerk at both ends, their cubic Hermite
+ *   interpolant's 2nd and 3rd derivatives a2, a3 at t1),
+ *   sqrt(eta4 (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)), and its 6th-order
  *   generalisation eta6 ((|a||s| + |j|^2) / (|c||q| + |p|^2))^(1/6),
  *   quantised as above (Sec. 3.7 uses eta4 = 0.01, eta6 = 0.1).
  * A new step at the 2^-50 floor stops the run after that block with

@@ -356,20 +356,26 @@ def hermite6_shared(m, x, v, eps2: float, dt: float, n_steps: int):
     return x, v
 
 
-def _h6_step_want(eta4, eta6, a1, j1, s1, c1, p1, q):
-    """Next step of a particle from the end-of-step derivatives: the average
-    of Aarseth's 4th-order criterion and the 6th-order generalisation
-    (Nitadori & Makino 2008),
-        dt4 = sqrt(eta4 (|a||s| + |j|^2) / (|j||c| + |s|^2))
-        dt6 = eta6 ((|a||s| + |j|^2) / (|c||q| + |p|^2))^(1/6)."""
+def _h6_step_want(eta4, eta6, h, a0, j0, a1, j1, s1, c1, p1, q):
+    """Next step of a particle from the end of its step: the average of
+    Aarseth's 4th-order criterion, evaluated as the 4th-order scheme does
+    (a and jerk at both ends; the 2nd and 3rd derivatives at t1 of their cubic
+    Hermite interpolant, as in hermite4_block),
+        dt4 = sqrt(eta4 (|a1||a2| + |j1|^2) / (|j1||a3| + |a2|^2)),
+    and its 6th-order generalisation (Nitadori & Makino 2008) with the pass's
+    snap and the quintic interpolant's crackle c1, pop p1 and 5th derivative q,
+        dt6 = eta6 ((|a1||s1| + |j1|^2) / (|c1||q| + |p1|^2))^(1/6)."""
+    h2 = h * h
+    a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) / (h2 * h)
+    a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) / h2 + h * a3
     A, J, S = np.linalg.norm(a1), np.linalg.norm(j1), np.linalg.norm(s1)
+    A2, A3 = np.linalg.norm(a2), np.linalg.norm(a3)
     C, P, Q = np.linalg.norm(c1), np.linalg.norm(p1), np.linalg.norm(q)
-    num = A * S + J * J
-    d4 = J * C + S * S
+    d4 = J * A3 + A2 * A2
     d6 = C * Q + P * P
     if not (d4 > 0.0 and d6 > 0.0):
         return math.inf
-    return 0.5 * (math.sqrt(eta4 * num / d4) + eta6 * (num / d6) ** (1.0 / 6.0))
+    return 0.5 * (math.sqrt(eta4 * (A * A2 + J * J) / d4) + eta6 * ((A * S + J * J) / d6) ** (1.0 / 6.0))
 
 
 def hermite6_block(m, x, v, eps2: float, t_end: float, eta4: float, eta6: float, eta_s: float,
@@ -408,11 +414,13 @@ def hermite6_block(m, x, v, eps2: float, t_end: float, eta4: float, eta6: float,
         f = forces(ids[act], xp[act], vp[act], ids, m, xp, vp, eps2, 6, ai=ap[act], aj=ap)
         a1, j1, s1 = f["acc"], f["jerk"], f["snap"]
         h = hh[act]
-        x1, v1, c1, p1, q = _h6_correct(h, x[act], v[act], a[act], j[act], s[act], a1, j1, s1)
+        a0, j0 = a[act].copy(), j[act].copy()
+        x1, v1, c1, p1, q = _h6_correct(h, x[act], v[act], a0, j0, s[act], a1, j1, s1)
         x[act], v[act], a[act], j[act], s[act], c[act], t[act] = x1, v1, a1, j1, s1, c1, t1
         for k, i in enumerate(act):
-            want = _h6_step_want(eta4, eta6, a1[k], j1[k], s1[k], c1[k], p1[k], q[k])
-            dt[i] = _quantise(want, min(2.0 * float(h[k, 0]), dt_max), t1)
+            hk = float(h[k, 0])
+            want = _h6_step_want(eta4, eta6, hk, a0[k], j0[k], a1[k], j1[k], s1[k], c1[k], p1[k], q[k])
+            dt[i] = _quantise(want, min(2.0 * hk, dt_max), t1)
         steps += 1
         active_sum += len(act)
     return x, v, t, {"block_steps": steps, "active_sum": active_sum, "dt": dt}

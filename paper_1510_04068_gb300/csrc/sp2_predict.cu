@@ -384,16 +384,20 @@ __global__ void block_correct_dev_kernel(JStore js, double *dt, const int32_t *a
 //   c1 h^3 = 60 (a1 - a0) - 24 h j0 - 36 h j1 - 3 h^2 s0 + 9 h^2 s1
 //   p1 h^4 = 360 (a1 - a0) - 168 h j0 - 192 h j1 - 24 h^2 s0 + 36 h^2 s1
 //   q  h^5 = 720 (a1 - a0) - 360 h (j0 + j1) - 60 h^2 (s0 - s1).
-// The next step is the mean of Aarseth's criterion (eta4 inside the root)
-// and its 6th-order generalisation (eta6 times the sixth root), quantised
-// like the 4th-order one.
+// The next step is the mean of Aarseth's criterion (eta4 inside the root),
+// evaluated as the 4th-order scheme does from a and jerk at both ends (the
+// 2nd and 3rd derivatives at t1 of their cubic Hermite interpolant), and its
+// 6th-order generalisation (eta6 times the sixth root) with the pass's snap
+// and the quintic interpolant's crackle, pop and 5th derivative, quantised
+// like the 4th-order step.  Only the 6th-order half sees the h^-5
+// amplification of force noise in the interpolated derivatives.
 __device__ __forceinline__ void correct6_one(const JStore &js, double *dt, int64_t s, int64_t k, double t1,
                                              const double *a1, const double *j1, const double *s1, double eta4,
                                              double eta6, double dt_max) {
     const double h = t1 - js.t[s];
     const double h2 = h * h, h3 = h2 * h;
     const double ih3 = 1.0 / h3, ih4 = ih3 / h, ih5 = ih4 / h;
-    double an[3], jn[3], sn[3], cn[3], pn[3], qn[3];
+    double an[3], jn[3], sn[3], cn[3], pn[3], qn[3], a2[3], a3[3];
     for (int c = 0; c < 3; ++c) {
         const int64_t q = 3 * s + c;
         const double x0 = js.x[q], v0 = js.v[q], a0 = js.a[q], j0 = js.jk[q], s0 = js.sn[q];
@@ -404,6 +408,8 @@ __device__ __forceinline__ void correct6_one(const JStore &js, double *dt, int64
         cn[c] = (60.0 * da - h * (24.0 * j0 + 36.0 * jj) + h2 * (9.0 * ss - 3.0 * s0)) * ih3;
         pn[c] = (360.0 * da - h * (168.0 * j0 + 192.0 * jj) + h2 * (36.0 * ss - 24.0 * s0)) * ih4;
         qn[c] = (720.0 * da - 360.0 * h * (j0 + jj) - 60.0 * h2 * (s0 - ss)) * ih5;
+        a3[c] = (12.0 * (a0 - aa) + 6.0 * h * (j0 + jj)) / h3;
+        a2[c] = (-6.0 * (a0 - aa) - h * (4.0 * j0 + 2.0 * jj)) / h2 + h * a3[c];
         an[c] = aa;
         jn[c] = jj;
         sn[c] = ss;
@@ -416,9 +422,11 @@ __device__ __forceinline__ void correct6_one(const JStore &js, double *dt, int64
     }
     js.t[s] = t1;
     const double A = norm3(an), J = norm3(jn), S = norm3(sn), C = norm3(cn), P = norm3(pn), Q = norm3(qn);
-    const double num = A * S + J * J, d4 = J * C + S * S, d6 = C * Q + P * P;
-    const double want = (d4 > 0.0 && d6 > 0.0) ? 0.5 * (sqrt(eta4 * num / d4) + eta6 * pow(num / d6, 1.0 / 6.0))
-                                               : dt_max;
+    const double A2 = norm3(a2), A3 = norm3(a3);
+    const double d4 = J * A3 + A2 * A2, d6 = C * Q + P * P;
+    const double want = (d4 > 0.0 && d6 > 0.0)
+                            ? 0.5 * (sqrt(eta4 * (A * A2 + J * J) / d4) + eta6 * pow((A * S + J * J) / d6, 1.0 / 6.0))
+                            : dt_max;
     dt[s] = quantise_dt(want, fmin(2.0 * h, dt_max), t1);
     if (js.dsc) write_dscache(js, s);
 }

@@ -106,3 +106,29 @@ def test_block_steps_and_energy(oracle_mod):
     x4, v4, _, st4 = oracle_mod.hermite4_block(m, x, v, eps2, 2.0 ** -3, 0.01, 0.01, 2.0 ** -5)
     e4 = abs(oracle_mod.energy(m, x4, v4, eps2) / e0 - 1.0)
     assert errs[1] < e4 / 100
+
+
+def test_criterion_survives_force_noise(oracle_mod, monkeypatch):
+    """Force noise of the size of double-single forces (3e-8 of the scale
+    sums, added in the oracle on the CPU) costs the 6th-order block scheme
+    some extra blocks but does not collapse its steps: the 4th-order half of
+    the averaged criterion comes from a and jerk alone, whose interpolation
+    amplifies the noise least (Sec. 3.7 warns that noisy jerk and snap can
+    drive the 6th-order step to zero)."""
+    n, eps2, t_end, dt_max = 256, 1e-6, 2.0 ** -4, 1.0 / 16
+    m, x, v = W.plummer(n, 21)
+    _, _, _, clean = oracle_mod.hermite6_block(m, x, v, eps2, t_end, 0.01, 0.1, 0.01, dt_max)
+    exact = oracle_mod.forces
+    rng = np.random.default_rng(5)
+
+    def noisy(*args, **kw):
+        f = exact(*args, **kw)
+        for key, sc in (("acc", "sc_acc"), ("jerk", "sc_jerk"), ("snap", "sc_snap")):
+            f[key] = f[key] + 3e-8 * f[sc][:, None] * rng.standard_normal(f[key].shape) / np.sqrt(3.0)
+        return f
+
+    monkeypatch.setattr(oracle_mod, "forces", noisy)
+    _, _, t, st = oracle_mod.hermite6_block(m, x, v, eps2, t_end, 0.01, 0.1, 0.01, dt_max)
+    assert np.all(t == t_end)
+    assert clean["block_steps"] <= st["block_steps"] < 3 * clean["block_steps"], (clean["block_steps"], st)
+    assert st["dt"].min() > 2.0 ** -20
