@@ -334,6 +334,12 @@ def run_ours(args, world, rank, local):
     peak_tops = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
     achieved = inter_step * OPS_PER_INTERACTION / (force_ms / 1e3) / 1e12
     clocks = clk.summary()
+    # measured pipe rates (after the timed region): a second denominator for
+    # the FMA-pipe fraction next to the one derived from unit counts and clock
+    try:
+        pipes = sp2.measure_pipe_peaks()
+    except sp2.SP2Error:
+        pipes = None
     tb, _sha = committed_traffic()
     traffic = tb if (tb is not None and n == 131072 and n_act == 131072) else None
 
@@ -356,7 +362,15 @@ def run_ours(args, world, rank, local):
                      "kernel": "pass_kernel<MixedPairForce<4,NN>>", "force_ms_per_launch": force_ms,
                      "ops_per_interaction": OPS_PER_INTERACTION,
                      "peak_basis": f"{dev_props.multi_processor_count} SMs x 128 FMA-pipe lanes x {sm_max:.0f} MHz "
-                                   f"(max SM clock, MEASURED_PEAKS.json)"},
+                                   f"(max SM clock, MEASURED_PEAKS.json)",
+                     "measured_pipe_peaks": None if pipes is None else {
+                         "fp32_fma_lane_tops": pipes["fp32_fma_lane_ops"] / 1e12,
+                         "fp32x2_fma_lane_tops": pipes["fp32x2_fma_lane_ops"] / 1e12,
+                         "fp64_fma_tops": pipes["fp64_fma_ops"] / 1e12,
+                         "rsqrt_tops": pipes["rsqrt_ops"] / 1e12,
+                         "probe": "sp2_measure_pipe_peaks: independent FFMA / f32x2 FMA / DFMA / MUFU rsqrt chains"},
+                     "frac_of_measured_fma": None if pipes is None else achieved / (
+                         max(pipes["fp32_fma_lane_ops"], pipes["fp32x2_fma_lane_ops"]) / 1e12)},
         "gpu_launches": launches,
         "clocks": clocks,
     }

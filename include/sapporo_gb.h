@@ -353,6 +353,23 @@ sp2_status sp2_sync(sp2_ctx *ctx);
 sp2_status sp2_profile_reset(sp2_ctx *ctx);
 sp2_status sp2_profile_read(sp2_ctx *ctx, int64_t *counts, double *total_ms, int n_stages);
 
+/* Measured pipe rates of the current device (a measurement utility; the
+ * paper has none): independent chains of one operation per thread, 8 CTAs of
+ * 256 threads per SM, one warm-up and one timed launch each (10-50 ms), on a
+ * stream of its own, synchronous.  The rates are operations per second at
+ * whatever clock the GPU ran: FP32 FMA lane-operations issued as scalar FFMA
+ * and as packed f32x2 FMA (two lane-operations per lane and instruction),
+ * FP64 FMAs, and MUFU reciprocal square roots.  The force kernels' FMA-pipe
+ * roofline is quoted against the larger FP32 rate.  Errors: SP2_ERR_ARG
+ * (null), SP2_ERR_CUDA. */
+typedef struct {
+    double fp32_fma_lane_ops;
+    double fp32x2_fma_lane_ops;
+    double fp64_fma_ops;
+    double rsqrt_ops;
+} sp2_pipe_peaks;
+sp2_status sp2_measure_pipe_peaks(sp2_pipe_peaks *out);
+
 /* Number of kernels the library has launched on this context since it opened
  * (memset / memcpy nodes excluded). */
 int64_t sp2_kernel_launches(const sp2_ctx *ctx);

@@ -85,6 +85,7 @@ _SIGS = [
     ("sp2_profile_reset", [_P], c_int),
     ("sp2_profile_read", [_P, POINTER(c_int64), POINTER(c_double), c_int], c_int),
     ("sp2_kernel_launches", [_P], c_int64),
+    ("sp2_measure_pipe_peaks", [_P], c_int),
     ("sp2_info", [_P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int)], c_int),
     ("sp2_step_static", [c_int64, _P, _P, _P, _P, _P, _P, _P, c_double, c_double, c_int64, _P, _P, _P, _P, _P, _P,
                          _P], c_int),
@@ -217,6 +218,18 @@ def sp2_compute_ext(ctx, xi, vi=None, ai=None, i_slot=None, acc=None, jerk=None,
     ptrs, kind, _k = _marshal([i_slot, xi, vi, ai, acc, jerk, snap, pot, nn_id, nn_r2],
                               [I4, F8, F8, F8, F8, F8, F8, F8, I4, F8])
     _check(load().sp2_compute_ext(ctx, len(xi), *ptrs, kind), ctx)
+
+
+class sp2_pipe_peaks(Structure):
+    _fields_ = [("fp32_fma_lane_ops", c_double), ("fp32x2_fma_lane_ops", c_double), ("fp64_fma_ops", c_double),
+                ("rsqrt_ops", c_double)]
+
+
+def measure_pipe_peaks():
+    """Measured pipe rates of the current device (operations per second)."""
+    pk = sp2_pipe_peaks()
+    _check(load().sp2_measure_pipe_peaks(byref(pk)))
+    return {name: getattr(pk, name) for name, _ in pk._fields_}
 
 
 class sp2_block_stats(Structure):

@@ -252,3 +252,21 @@ def test_outputs_not_written_past_their_end(precision):
             assert np.all(tail == (-77 if k == "nn_id" else 7.25)), (n_i, shape, k)
             assert np.all(np.isfinite(b[:n_i * w].cpu().numpy().astype(np.float64))), (n_i, k)
     c.close()
+
+
+@pytest.mark.gpu
+def test_pipe_peak_probe():
+    """The pipe-rate probe returns finite rates in the range a GB300 can have
+    (152 SMs, <= 2.1 GHz): FP32 FMA lanes 5-50 T/s in both forms, FP64 FMA
+    0.05-5 T/s, rsqrt 0.5-20 T/s."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_04068_gb300 import build, sp2
+    build.build()
+    sp2.load()
+    pk = sp2.measure_pipe_peaks()
+    assert 5e12 < pk["fp32_fma_lane_ops"] < 5e13, pk
+    assert 5e12 < pk["fp32x2_fma_lane_ops"] < 5e13, pk
+    assert 5e10 < pk["fp64_fma_ops"] < 5e12, pk
+    assert 5e11 < pk["rsqrt_ops"] < 2e13, pk
