@@ -113,6 +113,12 @@ int main(void) {
     cfg.order = 3;
     if (sp2_open(&ctx, &cfg) != SP2_ERR_ARG || ctx != NULL) return 1;
     if (sp2_close(NULL) != SP2_OK) return 2;
+    {
+        sp2_block_stats st;
+        if (sp2_block_run(NULL, 1.0, 0.01, 0.0625, &st) != SP2_ERR_ARG) return 3;
+        if (sp2_block_run_h6(NULL, 1.0, 0.01, 0.1, 0.0625, &st) != SP2_ERR_ARG) return 4;
+        if (sp2_measure_pipe_peaks(NULL) != SP2_ERR_ARG) return 5;
+    }
     printf("%s\n", sp2_strerror(SP2_ERR_RANGE));
     return 0;
 }
