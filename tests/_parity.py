@@ -1,7 +1,9 @@
 """Shared helpers of the GPU parity tests: seeded inputs, the library call, and
 the tolerance checks against the oracle.
 
-Tolerances (BASELINE targets; the reading of "relative" is stated in the design doc):
+Tolerances (errors of acc, jerk and snap are taken relative to the per-sink
+scale sums, the sum over sources of each term's magnitude; of pot relative to
+|pot|, whose terms share one sign):
   FP64 mode:   acc, jerk, snap: |d| / scale sum <= 1e-12; pot: |d| / |pot| <= 1e-12;
                nearest-neighbour id exact (ties go to the smaller id on both sides);
                nn_r2 bit-compatible (<= 1e-15 relative).
