@@ -382,7 +382,7 @@ sp2_status sp2_info(const sp2_ctx *ctx, int64_t *n_loaded, int64_t *n_max, int *
  * The paper has no counterpart; this entry point exists for callers that
  * cannot allocate device memory where they need forces -- work being captured
  * into a CUDA graph, hosts whose device memory belongs to an allocator or
- * budget they may not bypass, loops that must not enter the driver's
+ * budget they may not bypass, loops that must not enter the CUDA
  * allocator.  Its scratch (predicted records, per-slice partial sums, the
  * work-queue counter) is one fixed 16 MiB array inside the library, which every
  * GPU that loads the library keeps until the process exits; the call itself

@@ -7,7 +7,7 @@
 // force evaluation: code running inside a CUDA stream capture (allocation is
 // not captured), hosts whose device memory is owned by another allocator or
 // budget they may not bypass, or real-time / signal-driven loops that must not
-// enter the driver's allocator.  They pass inputs and outputs; everything else
+// enter the CUDA allocator.  They pass inputs and outputs; everything else
 // lives in `sp2_static_scratch`.
 //
 // The array is kStaticScratchBytes per GPU that loads the library, held until

@@ -3,7 +3,7 @@ entry points (sp2_set_j + sp2_predict + sp2_compute), on two calls in a row.
 
 Callers that cannot allocate device memory where they need forces -- inside a
 CUDA stream capture, under a host allocator they may not bypass, or in loops
-that must not enter the driver's allocator -- use sp2_step_static, whose scratch
+that must not enter the CUDA allocator -- use sp2_step_static, whose scratch
 is a fixed array inside the library.  This file is collected last on purpose:
 if it fails, a run that stops at the first failure has run everything else."""
 import ctypes
