@@ -21,6 +21,9 @@ Contents
                       Makino 2008; crackle in the predictor; test driver)
 ``hermite6_block``    block time-step 6th-order Hermite integrator with the
                       averaged 4th/6th-order criterion (Sec. 3.7; test driver)
+``hermite3_derivs``   a2(t1), a3 of the cubic Hermite interpolant of a step
+``aarseth4``          Aarseth's 4th-order time-step criterion
+``aarseth6``          its 6th-order generalisation (Nitadori & Makino 2008)
 ``adjoint``           float64 torch restatement for gradient checks (adjoint.py)
 
 Parity status: every output is pinned by the ``-m "not gpu"`` tests
@@ -28,7 +31,9 @@ Parity status: every output is pinned by the ``-m "not gpu"`` tests
 Newton's third law, pair-sum symmetry, finite differences along the predictor,
 invariances, Hermite energy conservation, 6th-order Hermite exactness on a
 quintic and 6th-order convergence on a Kepler orbit; neighbour lists against scipy's
-pairwise distances on an exact integer grid, symmetry, strictness, overflow).
+pairwise distances on an exact integer grid, symmetry, strictness, overflow;
+the time-step criteria in closed form on a circular orbit, the interpolated
+derivatives exact on a cubic and convergent on an eccentric Kepler orbit).
 """
 from __future__ import annotations
 
@@ -239,6 +244,47 @@ def _quantise(want, cap, t1):
     return d
 
 
+def hermite3_derivs(h, a0, j0, a1, j1):
+    """2nd derivative at t1 and (constant) 3rd derivative of the cubic Hermite
+    interpolant of the acceleration through (a0, j0) at t0 and (a1, j1) at
+    t1 = t0 + h (h a column of per-row steps, or a scalar):
+        a2(t0) = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2
+        a3     = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3,   a2(t1) = a2(t0) + h a3.
+    Returns (a2(t1), a3)."""
+    h2 = h * h
+    a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) / (h2 * h)
+    a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) / h2 + h * a3
+    return a2, a3
+
+
+def aarseth4(eta, a, j, a2, a3):
+    """Aarseth's 4th-order time-step criterion (the one Sec. 3.7's averaged
+    criterion starts from) for one particle, from its acceleration a, jerk j,
+    2nd and 3rd derivatives a2, a3 (3-vectors):
+        dt = sqrt(eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)),
+    eta inside the root.  +inf when the denominator vanishes."""
+    A, J = float(np.linalg.norm(a)), float(np.linalg.norm(j))
+    A2, A3 = float(np.linalg.norm(a2)), float(np.linalg.norm(a3))
+    den = J * A3 + A2 * A2
+    if not den > 0.0:
+        return math.inf
+    return math.sqrt(eta * (A * A2 + J * J) / den)
+
+
+def aarseth6(eta, a, j, s, c, p, q):
+    """The 6th-order generalisation of Aarseth's criterion (Nitadori & Makino
+    2008) for one particle, from a, jerk j, snap s, crackle c, pop p and the
+    5th derivative q of its acceleration (3-vectors):
+        dt = eta ((|a||s| + |j|^2) / (|c||q| + |p|^2))^(1/6),
+    eta outside the root.  +inf when the denominator vanishes."""
+    A, J, S = float(np.linalg.norm(a)), float(np.linalg.norm(j)), float(np.linalg.norm(s))
+    C, P, Q = float(np.linalg.norm(c)), float(np.linalg.norm(p)), float(np.linalg.norm(q))
+    den = C * Q + P * P
+    if not den > 0.0:
+        return math.inf
+    return eta * ((A * S + J * J) / den) ** (1.0 / 6.0)
+
+
 def hermite4_block(m, x, v, eps2: float, t_end: float, eta: float, eta_s: float, dt_max: float):
     """Block time-step 4th-order Hermite integration (Sec. 3.7: individual
     power-of-two steps; Makino & Aarseth 1992 corrector; Aarseth's criterion).
@@ -249,12 +295,9 @@ def hermite4_block(m, x, v, eps2: float, t_end: float, eta: float, eta_s: float,
     the predicted state and the corrector
         v1 = v0 + (a0 + a1) h/2 + (j0 - j1) h^2/12
         x1 = x0 + (v0 + v1) h/2 + (a0 - a1) h^2/12       (h = t1 - t_i),
-    then the next step from Aarseth's criterion with the derivatives of the
-    Hermite interpolation,
-        a2(t0) = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2
-        a3     = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3,   a2(t1) = a2(t0) + h a3
-        dt     = sqrt(eta (|a1||a2(t1)| + |j1|^2) / (|j1||a3| + |a2(t1)|^2)),
-    quantised by _quantise with cap min(2h, dt_max).  Returns (x, v, t, stats).
+    then the next step from Aarseth's criterion (aarseth4) with a2(t1) and a3
+    of the cubic Hermite interpolant of the step (hermite3_derivs), quantised
+    by _quantise with cap min(2h, dt_max).  Returns (x, v, t, stats).
     """
     n = len(m)
     ids = np.arange(n, dtype=np.int32)
@@ -281,15 +324,11 @@ def hermite4_block(m, x, v, eps2: float, t_end: float, eta: float, eta_s: float,
         a0, j0 = a[act], j[act]
         v1 = v[act] + (a0 + a1) * (h / 2) + (j0 - j1) * (h2 / 12)
         x1 = x[act] + (v[act] + v1) * (h / 2) + (a0 - a1) * (h2 / 12)
-        a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) / (h2 * h)
-        a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) / h2 + h * a3
+        a2, a3 = hermite3_derivs(h, a0, j0, a1, j1)
         x[act], v[act], a[act], j[act], t[act] = x1, v1, a1, j1, t1
-        A, J = np.linalg.norm(a1, axis=1), np.linalg.norm(j1, axis=1)
-        A2, A3 = np.linalg.norm(a2, axis=1), np.linalg.norm(a3, axis=1)
         for k, i in enumerate(act):
-            den = J[k] * A3[k] + A2[k] * A2[k]
-            want = math.sqrt(eta * (A[k] * A2[k] + J[k] * J[k]) / den) if den > 0 else dt_max
-            dt[i] = _quantise(want, min(2.0 * float(h[k, 0]), dt_max), t1)
+            want = aarseth4(eta, a1[k], j1[k], a2[k], a3[k])
+            dt[i] = _quantise(want if math.isfinite(want) else dt_max, min(2.0 * float(h[k, 0]), dt_max), t1)
         steps += 1
         active_sum += len(act)
     return x, v, t, {"block_steps": steps, "active_sum": active_sum, "dt": dt}
@@ -365,17 +404,12 @@ def _h6_step_want(eta4, eta6, h, a0, j0, a1, j1, s1, c1, p1, q):
     and its 6th-order generalisation (Nitadori & Makino 2008) with the pass's
     snap and the quintic interpolant's crackle c1, pop p1 and 5th derivative q,
         dt6 = eta6 ((|a1||s1| + |j1|^2) / (|c1||q| + |p1|^2))^(1/6)."""
-    h2 = h * h
-    a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) / (h2 * h)
-    a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) / h2 + h * a3
-    A, J, S = np.linalg.norm(a1), np.linalg.norm(j1), np.linalg.norm(s1)
-    A2, A3 = np.linalg.norm(a2), np.linalg.norm(a3)
-    C, P, Q = np.linalg.norm(c1), np.linalg.norm(p1), np.linalg.norm(q)
-    d4 = J * A3 + A2 * A2
-    d6 = C * Q + P * P
-    if not (d4 > 0.0 and d6 > 0.0):
+    a2, a3 = hermite3_derivs(h, a0, j0, a1, j1)
+    dt4 = aarseth4(eta4, a1, j1, a2, a3)
+    dt6 = aarseth6(eta6, a1, j1, s1, c1, p1, q)
+    if not (math.isfinite(dt4) and math.isfinite(dt6)):
         return math.inf
-    return 0.5 * (math.sqrt(eta4 * (A * A2 + J * J) / d4) + eta6 * ((A * S + J * J) / d6) ** (1.0 / 6.0))
+    return 0.5 * (dt4 + dt6)
 
 
 def hermite6_block(m, x, v, eps2: float, t_end: float, eta4: float, eta6: float, eta_s: float,
