@@ -237,22 +237,62 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, n, budget_s=12.0):
+def host_cpu():
+    """CPU model string and logical core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                model = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.partition(":")[2].strip()
+                        break
+        except OSError:
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
+def cpu_baseline(w, n, budget_s=12.0, budget_1core_s=6.0):
+    """The oracle (as it stands) on a bounded sample of the sinks: once on all
+    host cores (the reported `value`), once on one core."""
     import oracle
     oracle.build()
     step = lambda k: oracle.step(w["t"], w["idx"][:k], w["ids"], w["m"], w["tj"], w["x"], w["v"], w["a"],  # noqa: E731
                                  w["jerk"], None, eps2=1e-8, order=4)
-    k0 = min(256, len(w["idx"]))
-    t0 = time.perf_counter()
-    step(k0)
-    rate = k0 * n / max(time.perf_counter() - t0, 1e-6)
-    k = int(min(len(w["idx"]), max(k0, budget_s * rate / n)))
-    t0 = time.perf_counter()
-    step(k)
-    dt = time.perf_counter() - t0
-    return {"value": k * n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+
+    def timed_sample(budget):
+        k0 = min(64, len(w["idx"]))
+        t0 = time.perf_counter()
+        step(k0)
+        rate = k0 * n / max(time.perf_counter() - t0, 1e-6)
+        k = int(min(len(w["idx"]), max(k0, budget * rate / n)))
+        t0 = time.perf_counter()
+        step(k)
+        return k, time.perf_counter() - t0
+
+    cores = oracle.threads()
+    k, dt = timed_sample(budget_s)
+    oracle.set_threads(1)
+    try:
+        k1, dt1 = timed_sample(budget_1core_s)
+    finally:
+        oracle.set_threads(cores)
+    model, nproc = host_cpu()
+    return {"value": k * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} of the {len(w['idx'])} active sinks against all {n} sources "
-                      f"(plus the predictor over all {n}), {dt:.1f} s"}
+                      f"(plus the predictor over all {n}), {dt:.1f} s",
+            "value_1core": k1 * n / dt1,
+            "sample_1core": f"{k1} sinks against all {n} sources on one core, {dt1:.1f} s",
+            "cpu_model": model, "nproc": nproc}
 
 
 def run_ours(args, world, rank, local):

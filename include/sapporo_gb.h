@@ -380,18 +380,21 @@ sp2_status sp2_info(const sp2_ctx *ctx, int64_t *n_loaded, int64_t *n_max, int *
 /* Allocation-free block step: predictor + mixed-precision Hermite-4 force pass
  * (+ source-split reduction) on caller-owned device arrays, with no context.
  * The paper has no counterpart; this entry point exists for callers that
- * cannot allocate device memory where they need forces -- work being captured
- * into a CUDA graph, hosts whose device memory belongs to an allocator or
- * budget they may not bypass, loops that must not enter the CUDA
- * allocator.  Its scratch (predicted records, per-slice partial sums, the
- * work-queue counter) is one fixed 16 MiB array inside the library, which every
- * GPU that loads the library keeps until the process exits; the call itself
- * allocates nothing.
+ * cannot allocate device memory where they need forces: hosts whose device
+ * memory belongs to an allocator or a fixed budget they may not bypass (an
+ * integrator embedded in a larger code that hands out all device memory
+ * itself), and real-time or signal-driven loops that must not enter the CUDA
+ * allocator, which may block or fail under memory pressure.  Its scratch
+ * (predicted records, per-slice partial sums, the work-queue counter) is one
+ * fixed 16 MiB array inside the library, which every GPU that loads the
+ * library keeps until the process exits; the call itself allocates nothing.
  *
  * Inputs (device, n_j <= 65536 sources): id[n_j], m[n_j], x/v/a/jerk[n_j x 3],
  * t_j[n_j]; predicted to t as sp2_predict does in SP2_MIXED (order 4).
- * Sinks: i_idx[n_i] slots in [0, n_j) (n_i <= 65536; an entry outside that range
- * is skipped and its outputs are undefined).  Outputs (device): acc, jerk
+ * Sinks: i_idx[n_i] slots in [0, n_j) (n_i <= 65536; an entry outside that
+ * range is skipped, and that sink's acc, jerk, pot and nn_r2 are set to NaN and
+ * its nn_id to -1, so a bad index is visible without a host read-back).
+ * Outputs (device): acc, jerk
  * [n_i x 3], pot[n_i] (required), nn_id[n_i], nn_r2[n_i] (both NULL or both
  * given).  Work is enqueued on cuda_stream (NULL: the legacy default stream);
  * the call returns without waiting.
@@ -399,7 +402,7 @@ sp2_status sp2_info(const sp2_ctx *ctx, int64_t *n_loaded, int64_t *n_max, int *
  * The first call on a device looks the array's address up for that device
  * (cudaGetSymbolAddress, with the device current); make that first call before
  * any stream capture.  Every call shares the array and it keeps the previous
- * call's contents (each call clears the counter it needs): calls whose GPU work
+ * call's contents (each call clears the counter and error word it needs): calls whose GPU work
  * overlaps -- on different streams or from different host threads -- race and
  * must be serialised.  Errors: SP2_ERR_RANGE (n_j or n_i above 65536, or the
  * partial sums would not fit), SP2_ERR_ARG (null input, t or eps2 not finite,

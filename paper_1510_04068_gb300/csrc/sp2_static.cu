@@ -4,17 +4,22 @@
 // in one file-scope device array instead of memory from cudaMalloc.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// force evaluation: code running inside a CUDA stream capture (allocation is
-// not captured), hosts whose device memory is owned by another allocator or
-// budget they may not bypass, or real-time / signal-driven loops that must not
-// enter the CUDA allocator.  They pass inputs and outputs; everything else
-// lives in `sp2_static_scratch`.
+// force evaluation: hosts whose device memory is owned by another allocator or
+// a fixed budget they may not bypass (an integrator embedded in a larger code
+// that hands out all device memory itself), or real-time / signal-driven loops
+// that must not enter the CUDA allocator, whose calls may block or fail under
+// memory pressure.  They pass inputs and outputs; everything else lives in
+// `sp2_static_scratch`.
 //
 // The array is kStaticScratchBytes per GPU that loads the library, held until
 // the process exits.  Every call shares it and it keeps the previous call's
-// contents: the work-queue counter is cleared by each call, and calls whose
-// GPU work overlaps (different streams, or different host threads on the same
-// device) race on it -- serialise them.
+// contents: the work-queue counter and error word are cleared by each call,
+// and calls whose GPU work overlaps (different streams, or different host
+// threads on the same device) race on it -- serialise them.
+//
+// A sink slot outside [0, n_j) is skipped by the force pass; a last small
+// kernel then writes NaN into that sink's acc, jerk, pot and nn_r2 and -1 into
+// its nn_id, so a bad index shows in the outputs without a host read-back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +61,23 @@ sp2_status scratch_for_current_device(void **out) {
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Outputs of sinks whose slot lies outside [0, n_j): NaN (nn_id -1).
+__global__ void mark_bad_sinks_kernel(const int32_t *i_idx, int64_t n_i, int64_t n_j, double *acc, double *jerk,
+                                      double *pot, int32_t *nn_id, double *nn_r2) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n_i) return;
+    const int32_t slot = i_idx[k];
+    if (slot >= 0 && slot < n_j) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int c = 0; c < 3; ++c) {
+        acc[3 * k + c] = nan;
+        jerk[3 * k + c] = nan;
+    }
+    pot[k] = nan;
+    if (nn_id) nn_id[k] = -1;
+    if (nn_r2) nn_r2[k] = nan;
+}
 
 }  // namespace
 
@@ -169,5 +191,8 @@ extern "C" sp2_status sp2_step_static(int64_t n_j, const int32_t *id, const doub
         r.nn_r2 = nn_r2;
         if (launch_reduce_kernel(key, r, s) != cudaSuccess) return SP2_ERR_CUDA;
     }
+    mark_bad_sinks_kernel<<<static_cast<unsigned>(ceil_div(n_i, 256)), 256, 0, s>>>(i_idx, n_i, n_j, acc, jerk_out,
+                                                                                    pot, nn_id, nn_r2);
+    if (cudaGetLastError() != cudaSuccess) return SP2_ERR_CUDA;
     return SP2_OK;
 }
