@@ -12,8 +12,13 @@ Prints one JSON line.  `value` is interactions/s (N_active x N per step,
 self pair counted) over all ranks with inputs resident in HBM; `e2e` is the
 same metric through the C ABI with pinned host buffers (host->device copy of
 the updated particles and sink list, device->host copy of every output,
-inside the timed region).  With --gpus N > 1 (torchrun) every rank runs an
-independent replica (weak scaling); there is no collective on the data path.
+inside the timed region).  With --gpus N > 1 (torchrun) the ranks split the
+sources (Sec. 2.2.3): every rank holds the same particle set, runs the pass
+for all sinks over its own block of sources, and one exchange per step
+(shards.combine: NCCL sum of the force fields, minimum of the nearest
+neighbour) gives every rank the full result; `value` is then the job's
+N_active x N per step over the slowest rank's time (strong scaling).
+--replicas runs N independent replicas instead (weak scaling, no collective).
 """
 from __future__ import annotations
 
@@ -60,6 +65,8 @@ def parse():
                    help="comma-separated secondary sections: c1, sweep, h6, batched, adjoint, nb, h2, blk, blk6")
     p.add_argument("--blk-t-end", type=float, default=0.25,
                    help="end time of the 4th-order block time-step line (blk)")
+    p.add_argument("--replicas", action="store_true",
+                   help="with --gpus N > 1: N independent replicas instead of the source split")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
@@ -305,8 +312,13 @@ def run_ours(args, world, rank, local):
     libbuild.build()
     sp2.load()
     dev = torch.device("cuda", local)
+    from paper_1510_04068_gb300 import shards
     n, n_act = args.n, args.n_active
-    w = make_workload(n, n_act, seed=rank)
+    # world > 1: the source split of Sec. 2.2.3 (every rank the same particle
+    # set, its own block of sources, one exchange per step), unless --replicas
+    jsplit = world > 1 and not args.replicas
+    w = make_workload(n, n_act, seed=0 if jsplit else rank)
+    j_range = shards.shard_range(n, rank, world) if jsplit else None
     D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
     idx_h = w["idx"]
     stream = torch.cuda.Stream(device=dev)
@@ -331,14 +343,18 @@ def run_ours(args, world, rank, local):
                                        ctas_per_sm=0))
             tuned = None
         else:
-            tuned = None if args.no_tune else ctx.autotune(n_act)
+            # the tuner times passes over all sources; a rank of the source
+            # split takes the default shape for its block
+            tuned = None if (args.no_tune or jsplit) else ctx.autotune(n_act)
         launch = ctx.get_launch(n_act)
 
         def step(k):
             ctx.set_j(0, upd["ids"], upd["m"], upd["x"], upd["v"], upd["a"], upd["jerk"], None, upd["tj"],
                       slots=idx)
             ctx.predict(w["t"] + k * 2.0 ** -20)
-            ctx.compute(idx, **out)
+            ctx.compute(idx, j_range=j_range, **out)
+            if jsplit:
+                shards.combine(out)
 
         for k in range(args.warmup):
             step(k)
@@ -364,15 +380,16 @@ def run_ours(args, world, rank, local):
         prof = ctx.profile_read()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = allmax(world, sum(step_ms))
-    inter_step = n_act * n
-    value = world * args.steps * inter_step / (total_ms / 1e3)
+    inter_step = n_act * n  # per rank and step (replicas) or for the whole job (source split)
+    value = (1 if jsplit else world) * args.steps * inter_step / (total_ms / 1e3)
+    rank_inter = inter_step * (j_range[1] - j_range[0]) / n if jsplit else inter_step
     fcount, fms = prof["force"]
     force_ms = fms / max(fcount, 1)
     dev_props = torch.cuda.get_device_properties(dev)
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_tops = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
-    achieved = inter_step * OPS_PER_INTERACTION / (force_ms / 1e3) / 1e12
+    achieved = rank_inter * OPS_PER_INTERACTION / (force_ms / 1e3) / 1e12
     clocks = clk.summary()
     # measured pipe rates (after the timed region): a second denominator for
     # the FMA-pipe fraction next to the one derived from unit counts and clock
@@ -386,12 +403,14 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+        "scaling": "strong" if jsplit else "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.precision == "mixed" else WORKLOAD.replace(
                        "mixed precision (double-single positions, FP32 terms, FP64 reduction)", "FP64"),
                    "n": n, "n_active": n_act, "order": 4, "precision": args.precision,
-                   "eps": 1e-4, "nearest_neighbour": True, "parallelism": f"replicas{world}",
+                   "eps": 1e-4, "nearest_neighbour": True,
+                   "parallelism": f"jsplit{world}" if jsplit else f"replicas{world}",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, outside the step events)",
                    "launch": launch, "autotuned": tuned is not None,
                    "wall_ms_incl_flush": 1e3 * (wall1 - wall0) / args.steps},
@@ -419,7 +438,7 @@ def run_ours(args, world, rank, local):
     if world == 1 and rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, n)
     if not args.no_e2e:
-        line["e2e"] = e2e(ctx, w, upd, out, args, stream)
+        line["e2e"] = e2e(ctx, w, upd, out, args, stream, j_range, world)
     if not args.no_extras and rank == 0:
         line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")), args.blk_t_end)
     ctx.close()
@@ -427,9 +446,12 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def e2e(ctx, w, upd, out, args, stream):
-    """Same step through the C ABI with pinned host buffers; copies in the timed region."""
+def e2e(ctx, w, upd, out, args, stream, j_range=None, world=1):
+    """Same step through the C ABI with pinned host buffers; copies in the timed
+    region.  Source split (j_range set): the rank's pass writes device outputs,
+    the exchange combines them, and the combined result is copied to the host."""
     import torch
+    from paper_1510_04068_gb300 import shards
     pin = lambda t: t.cpu().pin_memory()  # noqa: E731
     hu = {k: pin(v) for k, v in upd.items()}
     hidx = pin(torch.as_tensor(w["idx"]))
@@ -439,15 +461,25 @@ def e2e(ctx, w, upd, out, args, stream):
     def step(k):
         ctx.set_j(0, hu["ids"], hu["m"], hu["x"], hu["v"], hu["a"], hu["jerk"], None, hu["tj"], slots=hidx)
         ctx.predict(w["t"] + k * 2.0 ** -20)
-        ctx.compute(hidx, **ho)
+        if j_range is None:
+            ctx.compute(hidx, **ho)
+        else:
+            upd_idx.copy_(hidx, non_blocking=True)
+            ctx.compute(upd_idx, j_range=j_range, **out)
+            shards.combine(out)
+            for key in out:
+                ho[key].copy_(out[key], non_blocking=True)
+            stream.synchronize()
 
     with torch.cuda.stream(stream):
+        upd_idx = torch.empty(hidx.shape, dtype=hidx.dtype, device=next(iter(out.values())).device)
         for k in range(max(1, args.warmup)):
             step(k)
+        barrier(world)
         t0 = time.perf_counter()
         for k in range(args.steps):
             step(k)
-        dt = time.perf_counter() - t0
+        dt = allmax(world, time.perf_counter() - t0)
     h2d = sum(v.numel() * v.element_size() for v in hu.values()) + 2 * hidx.numel() * 4
     d2h = sum(v.numel() * v.element_size() for v in ho.values())
     return {"value": args.steps * n_act * len(w["m"]) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

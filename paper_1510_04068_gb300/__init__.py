@@ -2,6 +2,7 @@
 
 ``sp2``      -- the C-ABI binding (sp2_open, sp2_set_j, sp2_predict, sp2_compute, ...)
 ``autograd`` -- differentiable forces and checkpointed Hermite-4 trajectories
+``shards``   -- the source split over several processes (one GPU each) and its exchange
 ``build``    -- in-tree nvcc build of libsapporo_gb.so
 """
 from . import sp2  # noqa: F401

@@ -94,6 +94,13 @@ struct is_paired { static constexpr bool value = false; };
 template <class P>
 struct is_paired<P, decltype(void(P::kPaired))> { static constexpr bool value = P::kPaired; };
 
+// Cache words a policy's fused prediction loads per source (1 for policies
+// without fused prediction, as a placeholder size).
+template <class P, class = void>
+struct raw_words { static constexpr int value = 1; };
+template <class P>
+struct raw_words<P, decltype(void(P::kRawWords))> { static constexpr int value = P::kRawWords; };
+
 // Lexicographic (r2, id) minimum; id -1 means "none" and only pairs with r2 = +inf.
 __device__ __forceinline__ void nn_merge(double &d, int &id, double od, int oid) {
     if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) {
@@ -172,6 +179,20 @@ struct MixedForce {
         Rec r;
 #pragma unroll
         for (int w = 0; w < NW; ++w) r.w[w] = o[w];
+        return r;
+    }
+    // the same in two steps: the cache words of source j (kRawWords float4s),
+    // then the record from those words
+    static constexpr int kRawWords = dscache_words(ORDER);
+    __device__ static __forceinline__ void fetch_raw(const float4 *dsc, int64_t j, float4 *w) {
+        ds_fetch<ORDER>(dsc, j, w);
+    }
+    __device__ static __forceinline__ Rec predict_raw(const float4 *w, float t_hi, float t_lo) {
+        float4 o[4];
+        predict_ds_words<ORDER>(w, t_hi, t_lo, o);
+        Rec r;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) r.w[k] = o[k];
         return r;
     }
     __device__ static __forceinline__ void sink_from(const Rec &r, Sink &s) {
@@ -950,44 +971,78 @@ __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *s
     }
 }
 
+// Source c of a tile as half (m & 1) of pair record (m >> 1) * jl + lj of q,
+// with lj = c & (jl - 1) and m = c / jl (the layout tile_loop reads).
+template <class P>
+__device__ __forceinline__ void put_pair_half(unsigned char *q, int c, int jl, const typename P::Rec &r) {
+    constexpr int W = P::RB / 16;
+    const int lj = c & (jl - 1), m = c / jl;
+    float *d = reinterpret_cast<float *>(q + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        d[8 * w] = r.w[w].x;
+        d[8 * w + 2] = r.w[w].y;
+        d[8 * w + 4] = r.w[w].z;
+        d[8 * w + 6] = r.w[w].w;
+    }
+}
+
+template <class P>
+__device__ __forceinline__ typename P::Rec filler_rec() {
+    constexpr int W = P::RB / 16;
+    typename P::Rec r;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint4 u = P::sentinel(w);
+        r.w[w] = *reinterpret_cast<const float4 *>(&u);
+    }
+    return r;
+}
+
 // Fused prediction of a tile: sources tb .. tb+cnt-1 predicted from the
 // double-single cache in global memory to t_hi + t_lo and written as pair
-// records (source c = lj + jl*m is half m & 1 of pair (m >> 1) * jl + lj);
-// the rest of the tile becomes filler records.  Two sources per thread and
-// step, both loaded and predicted before either is stored.
+// records; the rest of the tile becomes filler records.  Two sources per
+// thread and step, both loaded and predicted before either is stored.
 template <class P>
 __device__ __forceinline__ void predict_tile(const ForceParams &p, int64_t tb, int cnt, unsigned char *q, int jl) {
-    constexpr int W = P::RB / 16;
     const int nt = blockDim.x;
     for (int c0 = threadIdx.x; c0 < p.tile; c0 += 2 * nt) {
         typename P::Rec r[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = c0 + e * nt;
-            if (c < cnt) {
-                r[e] = P::predict(p.dsc, tb + c, p.t_hi, p.t_lo);
-            } else {
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    const uint4 u = P::sentinel(w);
-                    r[e].w[w] = *reinterpret_cast<const float4 *>(&u);
-                }
-            }
+            r[e] = (c < cnt) ? P::predict(p.dsc, tb + c, p.t_hi, p.t_lo) : filler_rec<P>();
         }
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = c0 + e * nt;
             if (c >= p.tile) break;
-            const int lj = c & (jl - 1), m = c / jl;
-            float *d = reinterpret_cast<float *>(q + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                d[8 * w] = r[e].w[w].x;
-                d[8 * w + 2] = r[e].w[w].y;
-                d[8 * w + 4] = r[e].w[w].z;
-                d[8 * w + 6] = r[e].w[w].w;
-            }
+            put_pair_half<P>(q, c, jl, r[e]);
         }
+    }
+}
+
+// The pipelined form for tiles of at most two sources per thread (c = tid and
+// tid + blockDim.x): fetch_tile loads the cache words of a tile's sources into
+// registers and returns at once; store_tile predicts them from there and
+// writes the pair records.  The pass issues the next tile's fetch before it
+// evaluates the current one, so its memory latency overlaps the arithmetic.
+template <class P>
+__device__ __forceinline__ void fetch_tile(const ForceParams &p, int64_t tb, int cnt, float4 (*raw)[P::kRawWords]) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int c = threadIdx.x + e * blockDim.x;
+        if (c < cnt) P::fetch_raw(p.dsc, tb + c, raw[e]);
+    }
+}
+template <class P>
+__device__ __forceinline__ void store_tile(const ForceParams &p, int cnt, const float4 (*raw)[P::kRawWords],
+                                           unsigned char *q, int jl) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int c = threadIdx.x + e * blockDim.x;
+        if (c >= p.tile) break;
+        put_pair_half<P>(q, c, jl, (c < cnt) ? P::predict_raw(raw[e], p.t_hi, p.t_lo) : filler_rec<P>());
     }
 }
 
@@ -1297,6 +1352,16 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             }
         }
 
+        // fused prediction with at most two sources of a tile per thread: the
+        // first tile's cache words are requested before the sinks are read
+        constexpr int kRaw = raw_words<P>::value;
+        float4 raw[2][kRaw];
+        const bool piped = FUSED && p.tile <= 2 * nt;
+        if constexpr (FUSED) {
+            if (piped && n_tiles > 0)
+                fetch_tile<P>(p, j0, (j0 + p.tile < j1) ? p.tile : static_cast<int>(j1 - j0), raw);
+        }
+
         typename P::Sink sk[IPT];
         typename P::Acc ac[IPT];
         bool val[IPT];
@@ -1334,8 +1399,18 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             const unsigned char *st;
             if constexpr (FUSED) {
                 __syncthreads();  // every thread has left the previous tile
-                predict_tile<P>(p, tb, (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb), pbuf, jl);
-                __syncthreads();
+                const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
+                if (piped) {
+                    store_tile<P>(p, cnt, raw, pbuf, jl);
+                    __syncthreads();
+                    if (t + 1 < n_tiles) {
+                        const int64_t nb = static_cast<int64_t>(tb) + p.tile;
+                        fetch_tile<P>(p, nb, (nb + p.tile < j1) ? p.tile : static_cast<int>(j1 - nb), raw);
+                    }
+                } else {
+                    predict_tile<P>(p, tb, cnt, pbuf, jl);
+                    __syncthreads();
+                }
                 st = pbuf;
             } else {
                 cp_async_wait<kStages - 2>();
@@ -1415,9 +1490,13 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             }
         }
         if (p.split > 1 && p.fused_reduce) {
-            __threadfence();  // this CTA's partials are visible device-wide before it is counted
+            // every partial of this CTA is written (barrier); thread 0's fence
+            // then makes them visible device-wide before the CTA is counted
             __syncthreads();
-            if (tid == 0) s_last = (atomicAdd(p.done + iblk, 1u) == static_cast<unsigned>(p.split - 1)) ? 1 : 0;
+            if (tid == 0) {
+                __threadfence();
+                s_last = (atomicAdd(p.done + iblk, 1u) == static_cast<unsigned>(p.split - 1)) ? 1 : 0;
+            }
             __syncthreads();
             if (s_last) {
                 __threadfence();

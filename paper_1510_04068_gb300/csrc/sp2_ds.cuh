@@ -43,27 +43,41 @@ __device__ __forceinline__ ds ds_split(double x) {
 }
 
 
-// Mixed-precision prediction of particle j from the double-single cache
-// (layout in sp2_internal.h): positions
+// Words of particle j's double-single cache entry (layout in sp2_internal.h)
+// that the predictor uses, loaded into w[0 .. dscache_words) (order 2: words
+// 0, 1 and 3 only).
+template <int ORDER>
+__device__ __forceinline__ void ds_fetch(const float4 *dsc, int64_t j, float4 *w) {
+    constexpr int W = (ORDER == 6) ? 8 : 7;
+    const float4 *q = dsc + j * W;
+    if (ORDER == 2) {
+        w[0] = __ldg(q);
+        w[1] = __ldg(q + 1);
+        w[3] = __ldg(q + 3);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) w[k] = __ldg(q + k);
+}
+
+// Mixed-precision prediction of a particle from the cache words ds_fetch
+// loaded: positions
 //   x_p = x + dt (v + dt (a/2 + dt (j/6 [+ dt s/24])))
 // with x, v, a/2 and dt double-single and the jerk / snap terms in FP32 (they
 // enter multiplied by dt^3, far below the double-single resolution of x);
 // velocities and accelerations leave as FP32.  Writes the predicted record's
 // 16-byte words {xh yh zh m}{xl yl zl id}{v 0}[{a 0}] to o[0..3].
 template <int ORDER>
-__device__ __forceinline__ void predict_ds_record(const float4 *dsc, int64_t j, float t_hi, float t_lo, float4 *o) {
-    constexpr int W = (ORDER == 6) ? 8 : 7;
-    const float4 *q = dsc + j * W;
+__device__ __forceinline__ void predict_ds_words(const float4 *w, float t_hi, float t_lo, float4 *o) {
     if (ORDER == 2) {  // leap-frog (GRAPE-5) sources are used where they are
-        const float4 w0 = q[0], w1 = q[1], w3 = q[3];
-        o[0] = w0;
-        o[1] = make_float4(w1.x, w1.y, w1.z, w3.w);
+        o[0] = w[0];
+        o[1] = make_float4(w[1].x, w[1].y, w[1].z, w[3].w);
         o[2] = o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    const float4 w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4], w5 = q[5], w6 = q[6];
+    const float4 w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4], w5 = w[5], w6 = w[6];
     float4 w7 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ORDER == 6) w7 = q[7];
+    if (ORDER == 6) w7 = w[7];
     const ds dt = ds_add({t_hi, t_lo}, {-w1.w, -w2.w});
     const float xh[3] = {w0.x, w0.y, w0.z}, xl[3] = {w1.x, w1.y, w1.z};
     const float vh[3] = {w2.x, w2.y, w2.z}, vl[3] = {w3.x, w3.y, w3.z};
@@ -86,6 +100,14 @@ __device__ __forceinline__ void predict_ds_record(const float4 *dsc, int64_t j, 
     o[1] = make_float4(ol[0], ol[1], ol[2], w3.w);
     o[2] = make_float4(ov[0], ov[1], ov[2], 0.f);
     o[3] = make_float4(oa[0], oa[1], oa[2], 0.f);
+}
+
+// Both steps for particle j of the cache.
+template <int ORDER>
+__device__ __forceinline__ void predict_ds_record(const float4 *dsc, int64_t j, float t_hi, float t_lo, float4 *o) {
+    float4 w[8];
+    ds_fetch<ORDER>(dsc, j, w);
+    predict_ds_words<ORDER>(w, t_hi, t_lo, o);
 }
 
 }  // namespace sp2

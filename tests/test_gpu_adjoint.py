@@ -241,12 +241,36 @@ def test_adjoint_vs_fd_oracle_size(torch_cuda, oracle_mod):
     assert np.linalg.norm(gs - fds) <= 1e-6 * np.linalg.norm(fds) + noise * np.sqrt(len(fds))
 
 
+def test_full_size_fp64_trajectory_matches_oracle(torch_cuda, oracle_mod):
+    """The anchor of the full-size gradient check below: at N = 16384, eps =
+    1e-3, 32 shared Hermite-4 steps of dt = 1/256, the library's FP64
+    trajectory (the one the central differences are taken on) is the oracle's
+    (hermite4_shared, 33 direct sums of 16384^2 pairs on the host cores) to
+    1e-12 relative in every final position and velocity."""
+    torch = torch_cuda
+    from paper_1510_04068_gb300 import autograd as AG
+    n, steps, dt, eps2 = 16384, 32, 1.0 / 256, 1e-6
+    m, x, v = W.plummer(n, 5)
+    xo, vo = oracle_mod.hermite4_shared(m, x, v, eps2, dt, steps)
+    sim64 = AG.HermiteSim(n, eps2, precision="fp64")
+    T = lambda q: torch.as_tensor(np.ascontiguousarray(q)).cuda()  # noqa: E731
+    with torch.no_grad():
+        xf, vf = sim64.trajectory(T(x), T(v), T(m), dt, steps, checkpoint_every=steps)
+    sim64.close()
+    xg, vg = xf.cpu().numpy(), vf.cpu().numpy()
+    ex = np.linalg.norm(xg - xo, axis=1) / np.linalg.norm(xo, axis=1)
+    ev = np.linalg.norm(vg - vo, axis=1) / np.linalg.norm(vo, axis=1)
+    print(f"FP64 trajectory vs oracle at N = {n}: max position {ex.max():.1e}, velocity {ev.max():.1e}")
+    assert ex.max() <= 1e-12 and ev.max() <= 1e-12, (float(ex.max()), float(ev.max()))
+
+
 def test_adjoint_full_size_vs_fp64_differences(torch_cuda):
     """N = 16384 Plummer, eps = 1e-3, 32 steps of dt = 1/256, checkpoints every
     8, mixed precision: the gradient of sum w . x_final agrees with central
-    differences (h = 1e-6) of the FP64 trajectory on 64 random coordinates
-    (the FP64 trajectory is the library's own FP64 path: a consistency
-    property at a size the CPU oracle cannot integrate in a test)."""
+    differences (h = 1e-6) of the FP64 trajectory on 64 random coordinates.
+    That trajectory is the library's FP64 path, which the test above ties to
+    the oracle's integrator at this size (64 coordinates x 2 oracle runs would
+    take ~20 minutes of host time)."""
     torch = torch_cuda
     from paper_1510_04068_gb300 import autograd as AG
     n, steps, dt, eps2 = 16384, 32, 1.0 / 256, 1e-6

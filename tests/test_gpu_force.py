@@ -161,7 +161,12 @@ def test_fused_prediction_small_n_active(sp2, oracle_mod, order):
         for n_i, shape, fused in ((1, dict(threads=32, i_per_thread=1, j_lanes=32, j_tile=256, split_j=40), True),
                                   (37, dict(threads=128, i_per_thread=1, j_lanes=2, j_tile=128, split_j=20), True),
                                   (37, dict(threads=32, i_per_thread=1, j_lanes=1, j_tile=64, split_j=20), False),
-                                  (300, dict(threads=256, i_per_thread=2, j_lanes=1, j_tile=128, split_j=9), True)):
+                                  (300, dict(threads=256, i_per_thread=2, j_lanes=1, j_tile=128, split_j=9), True),
+                                  # at most two sources per thread and tile: the next tile's cache words
+                                  # are fetched while the current one is evaluated (ragged last tiles)
+                                  (1, dict(threads=256, i_per_thread=1, j_lanes=32, j_tile=512, split_j=5), True),
+                                  (5, dict(threads=128, i_per_thread=1, j_lanes=16, j_tile=256, split_j=3), True),
+                                  (64, dict(threads=256, i_per_thread=1, j_lanes=4, j_tile=256, split_j=11), True)):
             idx = np.sort(np.random.default_rng(n_i).choice(n, n_i, replace=False)).astype(np.int32)
             c.predict(s["t"])
             c.set_launch(n_i, dict(shape, ctas_per_sm=0))

@@ -1,11 +1,14 @@
 """Two-rank (gloo, CPU) tests of the multi-rank path.
 
-A j-distributed run gives each rank a round-robin shard of the sources; every
-rank sums its shard's contributions for all sinks, and one exchange combines
-them: a sum of acc / jerk / pot and a lexicographic (r^2, id) minimum for the
-nearest neighbour.  The exchange is done here with torch.distributed on gloo and
-compared with the single-rank oracle.  The benchmark's replica timing (barrier,
-max over ranks) is exercised with the same process group."""
+A source-split run (Sec. 2.2.3) gives each rank a contiguous block of the
+sources (shards.shard_range); every rank sums its block's contributions for
+all sinks, and shards.combine exchanges them: a sum of acc / jerk / snap / pot
+and a lexicographic (r^2, id) minimum of the nearest neighbour, as
+torch.distributed collectives.  Here the ranks are CPU processes on gloo and
+each rank's partial comes from the oracle over its block (no GPU); the
+combined result must be the single-rank oracle's.  The benchmark's timing
+reduction (barrier, max over ranks) is exercised with the same process
+group."""
 import os
 import socket
 
@@ -31,49 +34,62 @@ def _worker(rank, world, port, out_dir):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import oracle
     import workloads as W
+    from paper_1510_04068_gb300 import shards
     oracle.set_threads(1)
-    n = 600
+    n = 601
     m, x, v = W.plummer(n, 11)
     a, jk, sn = W.derivative_noise(n, 12)
     ids = W.particle_ids(n, 13)
     tj = W.block_times(n, 14, 1.0)
     xp, vp, ap = oracle.predict(1.0, tj, x, v, a, jk, sn, 6)
-    sl = slice(rank, n, world)  # round-robin shard of the sources
+    lo, hi = shards.shard_range(n, rank, world)
+    sl = slice(lo, hi)
     part = oracle.forces(ids, xp, vp, ids[sl], m[sl], xp[sl], vp[sl], 1e-6, 6, ai=ap, aj=ap[sl])
-    summed = {}
-    for key in ("acc", "jerk", "snap", "pot"):
-        t = torch.as_tensor(part[key])
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        summed[key] = t.numpy()
-    r2 = torch.as_tensor(part["nn_r2"])
-    nid = torch.as_tensor(part["nn_id"].astype(np.int64))
-    g_r2 = [torch.empty_like(r2) for _ in range(world)]
-    g_id = [torch.empty_like(nid) for _ in range(world)]
-    dist.all_gather(g_r2, r2)
-    dist.all_gather(g_id, nid)
-    R2, ID = torch.stack(g_r2).numpy(), torch.stack(g_id).numpy()
-    best = np.lexsort((ID, R2), axis=0)[0]
-    nn_id = ID[best, np.arange(n)]
+    out = {k: torch.as_tensor(part[k]) for k in ("acc", "jerk", "snap", "pot", "nn_r2", "nn_id")}
+    shards.combine(out)
     # the benchmark's timing reduction: max over ranks
     sys.argv = ["bench.py"]
     import bench
     tmax = bench.allmax(world, float(rank + 1))
     bench.barrier(world)
+    res = {f"s_{k}": v.numpy() for k, v in out.items()}
+    # the neighbour exchange on hand-made shares: equal distances go to the
+    # smaller id, a rank without a neighbour (-1, +inf) loses to any rank with
+    # one, and no neighbour anywhere stays (-1, +inf)
+    inf = float("inf")
+    hand = {0: ([1.0, 2.0, inf, 4.0], [7, 3, -1, 8]), 1: ([1.0, 1.5, inf, inf], [5, 9, -1, -1])}
+    r2_h, id_h = hand.get(rank, ([inf] * 4, [-1] * 4))
+    tie = {"nn_r2": torch.tensor(r2_h, dtype=torch.float64), "nn_id": torch.tensor(id_h, dtype=torch.int32)}
+    shards.combine(tie)
+    res.update(tie_r2=tie["nn_r2"].numpy(), tie_id=tie["nn_id"].numpy())
+    np.savez(os.path.join(out_dir, f"res{rank}.npz"), tmax=tmax, lo=lo, hi=hi, **res)
     if rank == 0:
         full = oracle.forces(ids, xp, vp, ids, m, xp, vp, 1e-6, 6, ai=ap, aj=ap)
-        np.savez(os.path.join(out_dir, "res.npz"), tmax=tmax, nn_id=nn_id, full_nn=full["nn_id"],
-                 **{f"s_{k}": v for k, v in summed.items()}, **{f"f_{k}": full[k] for k in summed},
-                 sc_acc=full["sc_acc"], sc_jerk=full["sc_jerk"], sc_snap=full["sc_snap"])
+        np.savez(os.path.join(out_dir, "full.npz"), **full)
     dist.destroy_process_group()
 
 
-def test_two_rank_j_split_exchange(tmp_path):
+@pytest.mark.parametrize("world", [2, 3])
+def test_j_split_exchange(tmp_path, world):
     port = _free_port()
-    mp.start_processes(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
-    r = np.load(tmp_path / "res.npz")
-    assert float(r["tmax"]) == 2.0
-    for key, sc in (("acc", "sc_acc"), ("jerk", "sc_jerk"), ("snap", "sc_snap")):
-        err = np.linalg.norm(r[f"s_{key}"] - r[f"f_{key}"], axis=1) / r[sc]
-        assert err.max() <= 1e-14, key
-    assert np.allclose(r["s_pot"], r["f_pot"], rtol=1e-14, atol=0)
-    assert np.array_equal(r["nn_id"], r["full_nn"])
+    mp.start_processes(_worker, args=(world, port, str(tmp_path)), nprocs=world, join=True, start_method="spawn")
+    f = np.load(tmp_path / "full.npz")
+    blocks = []
+    for rank in range(world):
+        r = np.load(tmp_path / f"res{rank}.npz")
+        blocks.append((int(r["lo"]), int(r["hi"])))
+        assert float(r["tmax"]) == float(world)
+        for key, sc in (("acc", "sc_acc"), ("jerk", "sc_jerk"), ("snap", "sc_snap")):
+            err = np.linalg.norm(r[f"s_{key}"] - f[key], axis=1) / f[sc]
+            assert err.max() <= 1e-14, key
+        assert np.allclose(r["s_pot"], f["pot"], rtol=1e-14, atol=0)
+        # the neighbour is exact: every rank ends with the oracle's id and distance
+        assert np.array_equal(r["s_nn_id"], f["nn_id"])
+        assert np.array_equal(r["s_nn_r2"], f["nn_r2"])
+        assert r["tie_id"].tolist() == [5, 9, -1, 8]
+        assert r["tie_r2"].tolist() == [1.0, 1.5, float("inf"), 4.0]
+    assert blocks[0][0] == 0 and blocks[-1][1] == 601
+    assert all(blocks[k][1] == blocks[k + 1][0] for k in range(world - 1))
+    sizes = [hi - lo for lo, hi in blocks]
+    assert max(sizes) - min(sizes) <= 1
+
