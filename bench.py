@@ -67,6 +67,9 @@ def parse():
                    help="end time of the 4th-order block time-step line (blk)")
     p.add_argument("--replicas", action="store_true",
                    help="with --gpus N > 1: N independent replicas instead of the source split")
+    p.add_argument("--blk6-t-end", type=float, default=1.0,
+                   help="end time of the 6th-order block-step runs (Sec. 3.7 integrates one N-body time unit)")
+    p.add_argument("--blk6-n", default="16384", help="particle counts of the 6th-order block-step runs")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
@@ -440,7 +443,8 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         line["e2e"] = e2e(ctx, w, upd, out, args, stream, j_range, world)
     if not args.no_extras and rank == 0:
-        line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")), args.blk_t_end)
+        line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")), args.blk_t_end,
+                                args.blk6_t_end, tuple(int(q) for q in args.blk6_n.split(",")))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -501,7 +505,7 @@ def timed(fn, reps, stream):
     return statistics.median(ts)
 
 
-def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25):
+def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.0, blk6_n=(16384,)):
     """N_active sweep (mixed vs FP64), batched systems, adjoint: secondary lines."""
     import torch
     D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
@@ -524,7 +528,7 @@ def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25):
         if "blk" in sections:
             res["blk"] = bench_blk(sp2, dev, stream, t_end=blk_t_end)
         if "blk6" in sections:
-            res["blk6"] = bench_blk6(sp2, dev, stream)
+            res["blk6"] = [r for nb in blk6_n for r in bench_blk6(sp2, dev, stream, n=nb, t_end=blk6_t_end)]
     return res
 
 
@@ -778,12 +782,13 @@ def bench_blk(sp2, dev, stream, n=16384, t_end=0.25):
     return rows
 
 
-def bench_blk6(sp2, dev, stream, n=16384, t_end=0.03125):
+def bench_blk6(sp2, dev, stream, n=16384, t_end=1.0):
     """6th-order block time-steps with the averaged criterion (eta4 = 0.01,
-    eta6 = 0.1, steps <= 1/16; the scheme and parameters of Sec. 3.7) on a
-    Plummer sphere, eps = 1e-3, mixed and FP64: wall time, blocks, mean
-    N_active and the relative energy error at t_end (energies from an FP64
-    context of the library)."""
+    eta6 = 0.1, steps <= 1/16; the scheme and parameters of Sec. 3.7, one
+    N-body time unit by default) on a Plummer sphere, eps = 1e-3, mixed and
+    FP64: wall time, blocks, mean / min / max N_active and the relative energy
+    error at t_end (energies from an FP64 context of the library), or the
+    time at which a run stopped on the step-underflow guard."""
     import time
     import torch
     eps2 = 1e-6
@@ -813,8 +818,10 @@ def bench_blk6(sp2, dev, stream, n=16384, t_end=0.03125):
             st = c.block_run_h6(t_end, 0.01, 0.1, 1.0 / 16)
         except sp2.SP2Error as e:  # step underflow (the collapse Sec. 3.7 warns of for DS forces)
             torch.cuda.synchronize()
+            st = getattr(e, "stats", {})
             rows.append({"precision": name, "n": n, "t_end": t_end, "wall_s": time.perf_counter() - w0,
-                         "stopped": str(e)})
+                         "stopped": str(e), "stopped_at_t": st.get("t"), "block_steps": st.get("block_steps"),
+                         "mean_active": st.get("active_sum", 0) / max(st.get("block_steps") or 1, 1)})
             c.close()
             continue
         torch.cuda.synchronize()
@@ -824,6 +831,8 @@ def bench_blk6(sp2, dev, stream, n=16384, t_end=0.03125):
         c.close()
         rows.append({"precision": name, "n": n, "t_end": t_end, "wall_s": wall, "block_steps": st["block_steps"],
                      "mean_active": st["active_sum"] / max(st["block_steps"], 1),
+                     "min_active": st["min_active"], "max_active": st["max_active"],
+                     "us_per_block": 1e6 * wall / max(st["block_steps"], 1),
                      "interactions_per_s": st["active_sum"] * n / wall,
                      "energy_error": abs(energy(xs, vs) / e0 - 1.0)})
     return rows
@@ -861,12 +870,20 @@ def bench_batched(sp2, dev, stream):
                       nn_id=o["nn_id"][a:b], nn_r2=o["nn_r2"][a:b])
 
     s_ms = timed(per_system, 3, stream)
+    # the same 4096 per-system passes captured once and replayed as one CUDA
+    # graph: the launches' GPU-side cost without the host loop in between
+    sp2.sp2_graph_begin(c.ctx)
+    per_system()
+    gs = sp2.sp2_graph_end(c.ctx)
+    gs_ms = timed(lambda: sp2.sp2_graph_launch(c.ctx, gs), 5, stream)
+    sp2.sp2_graph_destroy(gs)
     sp2.sp2_graph_destroy(g)
     sp2.sp2_batch_plan_destroy(plan)
     c.close()
     inter = float(np.sum(np.diff(offsets) ** 2))
     return {"systems": 4096, "bodies": total, "interactions": inter, "batched_us": 1e3 * k_ms,
             "batched_graph_us_incl_predict": 1e3 * g_ms, "per_system_launches_us": 1e3 * s_ms,
+            "per_system_graph_us": 1e3 * gs_ms, "speedup_vs_per_system_graph": gs_ms / k_ms,
             "speedup_vs_per_system": s_ms / k_ms, "interactions_per_s": inter / (k_ms / 1e3)}
 
 

@@ -554,6 +554,48 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
 };
 
 // ---------------------------------------------------------------------------
+// The paired policy as the batched kernel runs it: the same interaction and
+// chunk fold, with the running double-single totals held in registers (the
+// batched kernel's systems are short and its totals per sink few) instead of
+// the pass kernel's shared-memory slots.
+// ---------------------------------------------------------------------------
+template <int ORDER, bool NN>
+struct MixedPairBatch : MixedPairForce<ORDER, NN> {
+    typedef MixedPairForce<ORDER, NN> Pair;
+    using Pair::NS;
+    struct Acc : Pair::Acc {
+        float th[NS];  // running totals, double-single (hi, lo)
+        float tl[NS];
+    };
+    __device__ static __forceinline__ void init(Acc &c) {
+        Pair::init(c);
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.th[f] = c.tl[f] = 0.f;
+    }
+    // level 2 (both halves added) -> the register totals by TwoSum (Knuth)
+    __device__ static __forceinline__ void flush(Acc &c, double *, int) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) {
+            const float v = c.g[f].x + c.g[f].y;
+            const float h = c.th[f] + v;
+            const float bv = h - c.th[f];
+            c.tl[f] += (c.th[f] - (h - bv)) + (v - bv);
+            c.th[f] = h;
+            c.g[f] = dup2(0.f);
+        }
+    }
+    __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(c.th[f]) + static_cast<double>(c.tl[f]);
+        t[NS - 1] = -t[NS - 1];
+    }
+    __device__ static __forceinline__ void nn_acc(const Acc &c, double &d, int &id) {
+        d = (NN && c.bid >= 0) ? static_cast<double>(c.bd) : d_inf();
+        id = NN ? c.bid : -1;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // FP64 force policy: every operation in IEEE double.  The unsoftened r^2 is
 // formed without fused multiply-adds, so that nearest-neighbour decisions are
 // taken on exactly the values a plain FP64 evaluation produces.
@@ -1656,7 +1698,7 @@ __device__ __forceinline__ void batch_tile_loop(const unsigned char *st, int tb,
 #pragma unroll
             for (int u = 2; u < P::kChunk; u += 2)
                 P::template interact2<SELF, false>(P::ld_pair(pq + (u >> 1) * P::PRB), tb + q0 + u, 1, u, sk, ac, eps2);
-            P::fold(ac, tb + q0);
+            P::fold(ac, tb + q0, pq, P::PRB, sk);
         }
     } else {
         for (int q0 = 0; q0 < n; q0 += P::kChunk) {
@@ -1742,7 +1784,7 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
         P::totals(ac, tot, 1, t);
         double nd;
         int nid;
-        if constexpr (has_fold_tile<P>::value) P::nn_acc(ac, nd, nid);
+        if constexpr (has_fold_tile<P>::value || is_paired<P>::value) P::nn_acc(ac, nd, nid);
         else P::nn(ac, sk, b.rec, static_cast<int64_t>(it.x) + it.y, 1, nd, nid);
         if (val) P::write_final(b, static_cast<int64_t>(slot) - b.out_base, t, nd, nid);
     }

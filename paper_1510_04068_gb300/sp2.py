@@ -256,8 +256,14 @@ def sp2_block_run(ctx, t_end, eta, dt_max):
 def sp2_block_run_h6(ctx, t_end, eta4, eta6, dt_max):
     """6th-order block time-steps to t_end (averaged criterion); statistics as a dict."""
     st = sp2_block_stats()
-    _check(load().sp2_block_run_h6(ctx, float(t_end), float(eta4), float(eta6), float(dt_max), byref(st)), ctx)
-    return {name: getattr(st, name) for name, _ in st._fields_}
+    status = load().sp2_block_run_h6(ctx, float(t_end), float(eta4), float(eta6), float(dt_max), byref(st))
+    stats = {name: getattr(st, name) for name, _ in st._fields_}
+    try:
+        _check(status, ctx)
+    except SP2Error as e:  # a stopped run (step underflow) still reports how far it got
+        e.stats = stats
+        raise
+    return stats
 
 
 def sp2_batch_plan_create(ctx, offsets):
