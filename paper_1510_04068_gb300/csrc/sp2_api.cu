@@ -267,12 +267,12 @@ struct PassOut {
 };
 
 // Dynamic shared memory of a pass launch (the kernel side computes the same):
-// the kStages-deep record ring (none when the prediction is fused: the pass
-// predicts each tile from global memory), for the mixed force passes one tile of
+// the kStages-deep record ring (of double-single cache words when the
+// prediction is fused: the pass predicts each tile in shared memory), for the mixed force passes one tile of
 // pair records, and for the mixed policies the 8-byte running totals of every
 // (thread, sink, field).
 size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
-    const size_t ring = fused ? 0 : static_cast<size_t>(kStagesDevice) * tile * rb;
+    const size_t ring = static_cast<size_t>(kStagesDevice) * tile * (fused ? 16 * dscache_words(order) : rb);
     const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
     const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
     return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);
@@ -315,8 +315,9 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     split = ceil_div(n_j, slice_len);
     const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
     const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused);
-    if (smem_total > 200 * 1024)
-        return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max 200 KiB)", smem_total);
+    if (smem_total > static_cast<size_t>(kMaxPassSmem))
+        return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max %d)", smem_total,
+                    kMaxPassSmem);
     if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
     int per_sm = L.ctas_per_sm;
     if (per_sm <= 0) {
@@ -1405,7 +1406,8 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         // the kernel run_pass will launch: fused prediction when the sinks fit one i-block
         const int fused = (mixed && c->js.dsc && n_i <= int64_t(L.threads / L.j_lanes) * L.i_per_thread) ? 1 : 0;
         KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread, fused};
-        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, fused) > 200 * 1024 ||
+        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, fused) >
+                static_cast<size_t>(kMaxPassSmem) ||
             force_kernel_occupancy(key, L.threads, L.j_tile, &occ) != cudaSuccess) {
             cudaGetLastError();
             return 0;
@@ -1534,6 +1536,9 @@ sp2_status sp2_sync(sp2_ctx *c) {
     if (flag) {
         SP2_CK(c, cudaMemsetAsync(c->dev_words + 1, 0, sizeof flag, c->stream));
         SP2_CK(c, cudaStreamSynchronize(c->stream));
+        if (flag & 2u)
+            return fail(c, SP2_ERR_TIMEOUT, "a bulk copy into shared memory did not complete within the wait limit "
+                                            "(outputs undefined)");
         return fail(c, SP2_ERR_RANGE, "a device-side slot index was outside the loaded set (skipped; outputs undefined)");
     }
     return SP2_OK;

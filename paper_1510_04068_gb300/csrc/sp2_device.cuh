@@ -37,6 +37,52 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Bulk asynchronous copies (TMA, no tensor map) into shared memory, completed
+// on an mbarrier: one thread arms the barrier with the byte count and issues
+// the copies; every thread then waits on the barrier's phase.
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make the barrier initialisation visible to the copy engine
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arm(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// bytes and both addresses multiples of 16
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}\n"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Wait for the barrier's phase `parity` to complete, giving up after
+// kMbarWaitLimit polls (each poll may suspend the thread for a short while).
+constexpr int kMbarWaitLimit = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    for (int it = 0; it < kMbarWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 __device__ __forceinline__ uint4 f4bits(float a, float b, float c, float d) {
     return make_uint4(__float_as_uint(a), __float_as_uint(b), __float_as_uint(c), __float_as_uint(d));
 }
@@ -1041,50 +1087,25 @@ __device__ __forceinline__ typename P::Rec filler_rec() {
     return r;
 }
 
-// Fused prediction of a tile: sources tb .. tb+cnt-1 predicted from the
-// double-single cache in global memory to t_hi + t_lo and written as pair
-// records; the rest of the tile becomes filler records.  Two sources per
-// thread and step, both loaded and predicted before either is stored.
+// Fused prediction of a tile whose double-single cache words (kRawWords
+// float4s per source, sources 0 .. cnt-1) a bulk copy has put in shared
+// memory at raw: every thread predicts sources tid, tid + blockDim.x, ... and
+// writes them as pair records; the rest of the tile becomes filler records.
 template <class P>
-__device__ __forceinline__ void predict_tile(const ForceParams &p, int64_t tb, int cnt, unsigned char *q, int jl) {
-    const int nt = blockDim.x;
-    for (int c0 = threadIdx.x; c0 < p.tile; c0 += 2 * nt) {
-        typename P::Rec r[2];
+__device__ __forceinline__ void predict_staged_tile(const ForceParams &p, const float4 *raw, int cnt,
+                                                    unsigned char *q, int jl) {
+    constexpr int RW = P::kRawWords;
+    for (int c = threadIdx.x; c < p.tile; c += blockDim.x) {
+        typename P::Rec r;
+        if (c < cnt) {
+            float4 w[RW];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int c = c0 + e * nt;
-            r[e] = (c < cnt) ? P::predict(p.dsc, tb + c, p.t_hi, p.t_lo) : filler_rec<P>();
+            for (int k = 0; k < RW; ++k) w[k] = raw[c * RW + k];
+            r = P::predict_raw(w, p.t_hi, p.t_lo);
+        } else {
+            r = filler_rec<P>();
         }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int c = c0 + e * nt;
-            if (c >= p.tile) break;
-            put_pair_half<P>(q, c, jl, r[e]);
-        }
-    }
-}
-
-// The pipelined form for tiles of at most two sources per thread (c = tid and
-// tid + blockDim.x): fetch_tile loads the cache words of a tile's sources into
-// registers and returns at once; store_tile predicts them from there and
-// writes the pair records.  The pass issues the next tile's fetch before it
-// evaluates the current one, so its memory latency overlaps the arithmetic.
-template <class P>
-__device__ __forceinline__ void fetch_tile(const ForceParams &p, int64_t tb, int cnt, float4 (*raw)[P::kRawWords]) {
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int c = threadIdx.x + e * blockDim.x;
-        if (c < cnt) P::fetch_raw(p.dsc, tb + c, raw[e]);
-    }
-}
-template <class P>
-__device__ __forceinline__ void store_tile(const ForceParams &p, int cnt, const float4 (*raw)[P::kRawWords],
-                                           unsigned char *q, int jl) {
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int c = threadIdx.x + e * blockDim.x;
-        if (c >= p.tile) break;
-        put_pair_half<P>(q, c, jl, (c < cnt) ? P::predict_raw(raw[e], p.t_hi, p.t_lo) : filler_rec<P>());
+        put_pair_half<P>(q, c, jl, r);
     }
 }
 
@@ -1154,11 +1175,11 @@ __device__ __forceinline__ void tile_loop(const unsigned char *st, int tb, int p
 // Merge the j-lanes of a sink (paired policies): the double-single totals
 // are combined with double-single adds and the nearest-neighbour candidates
 // (FP32 distances) with FP32 compares, so the xor-butterfly never waits on
-// the FP64 pipe; the merged totals leave as FP64.
+// the FP64 pipe; every lane ends with the sink's totals q[] (double-single)
+// and its nearest neighbour.
 template <class P>
-__device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, int jl, double *t, double &nd, int &nid) {
+__device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, int jl, ds *q, double &nd, int &nid) {
     const float2 *t2 = reinterpret_cast<const float2 *>(tot);
-    ds q[P::NS];
 #pragma unroll
     for (int f = 0; f < P::NS; ++f) q[f] = ds{t2[f * stride].x, t2[f * stride].y};
     float d = static_cast<float>(nd);  // exact: an FP32 distance or +inf
@@ -1175,10 +1196,48 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
             }
         }
     }
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) t[f] = static_cast<double>(q[f].h) + static_cast<double>(q[f].l);
-    t[P::NS - 1] = -t[P::NS - 1];
     nd = static_cast<double>(d);
+}
+
+// Where summed field f of sink i goes among the final outputs (null: not
+// requested): 0-2 acc, 3-5 jerk, 6-8 snap (order 6), NS-1 pot.
+template <class P>
+__device__ __forceinline__ double *final_field(const ForceParams &o, int64_t i, int f) {
+    if (f == P::NS - 1) return o.pot ? o.pot + i : nullptr;
+    if (f < 3) return o.acc ? o.acc + 3 * i + f : nullptr;
+    if (f < 6) return o.jerk ? o.jerk + 3 * i + (f - 3) : nullptr;
+    return o.snap ? o.snap + 3 * i + (f - 6) : nullptr;
+}
+
+// A sink's merged double-single totals leave as FP64 with the fields spread
+// over its jl lanes (lane lj takes fields lj, lj + jl, ...): each lane picks
+// its field with FP32 selects, so one conversion per round serves up to jl
+// fields -- GB300 runs FP64 at 1/64 of the FP32 rate.  Field f goes to the
+// final outputs (split == 1) or to the slice's partial-sum slot; the
+// potential field changes sign (its terms were summed as +m/r).
+template <class P>
+__device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i, int slice, const ds *q, int jl,
+                                                int lj) {
+    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+    for (int f0 = 0; f0 < P::NS; f0 += jl) {
+        const int f = f0 + lj;
+        float h = 0.f, l = 0.f;
+#pragma unroll
+        for (int g = 0; g < P::NS; ++g)
+            if (g == f) {
+                h = q[g].h;
+                l = q[g].l;
+            }
+        if (f < P::NS) {
+            double v = static_cast<double>(h) + static_cast<double>(l);
+            if (f == P::NS - 1) v = -v;
+            double *dst;
+            if (p.split == 1) dst = final_field<P>(p, i, f);
+            else if (p.sink_major) dst = p.part + (i * NF + f) * p.split + slice;
+            else dst = p.part + static_cast<int64_t>(f) * p.split * p.n_i + static_cast<int64_t>(slice) * p.n_i + i;
+            if (dst) *dst = v;
+        }
+    }
 }
 
 // FP64 reduction of one sink's slices (sink-major row: field f's slices are
@@ -1204,23 +1263,24 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
             on[q] = f0 + q * nw < P::NS;
             col[q] = row + static_cast<int64_t>(on[q] ? f0 + q * nw : f0) * split;
         }
+        // lane l adds slices l, l + 32, l + 64, ... in that order; the loads of
+        // 256 slices per field are all issued before the first add
         double v[4] = {0.0, 0.0, 0.0, 0.0};
-        int s = lane;
-        for (; s + 3 * 32 < split; s += 4 * 32) {
-            double x[4][4];
+        for (int s0 = 0; s0 < split; s0 += 8 * 32) {
+            double x[4][8];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) x[q][e] = on[q] ? __ldcg(col[q] + s + 32 * e) : 0.0;
+                for (int e = 0; e < 8; ++e) {
+                    const int s = s0 + lane + 32 * e;
+                    x[q][e] = (on[q] && s < split) ? __ldcg(col[q] + s) : 0.0;
+                }
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) v[q] += x[q][e];
+                for (int e = 0; e < 8; ++e)
+                    if (s0 + lane + 32 * e < split) v[q] += x[q][e];
         }
-        for (; s < split; s += 32)
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (on[q]) v[q] += __ldcg(col[q] + s);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -1234,23 +1294,18 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
         const double *col = row + static_cast<int64_t>(P::NS) * split;
         long long d = 0x7ff0000000000000LL;  // +inf
         int id = -1;
-        int s = lane;
-        for (; s + 7 * 32 < split; s += 8 * 32) {
+        for (int s0 = 0; s0 < split; s0 += 8 * 32) {
             long long xd[8];
             int xi[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                xd[q] = __double_as_longlong(__ldcg(col + s + 32 * q));
-                xi[q] = __ldcg(row_id + s + 32 * q);
+                const int s = s0 + lane + 32 * q;
+                xd[q] = (s < split) ? __double_as_longlong(__ldcg(col + s)) : 0x7ff0000000000000LL;
+                xi[q] = (s < split) ? __ldcg(row_id + s) : -1;
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q)
                 if (xd[q] < d || (xd[q] == d && static_cast<unsigned>(xi[q]) < static_cast<unsigned>(id))) { d = xd[q]; id = xi[q]; }
-        }
-        for (; s < split; s += 32) {
-            const long long od = __double_as_longlong(__ldcg(col + s));
-            const int oid = __ldcg(row_id + s);
-            if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -1358,11 +1413,38 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     const int per = p.tile / jl;  // a multiple of P::kChunk (host-checked)
     constexpr bool kPair = is_paired<P>::value;
     static_assert(kPair || !FUSED, "fused prediction needs a paired policy");
-    // fused prediction writes pair records straight from global memory and
-    // needs no staging ring
-    const size_t ring_stride = FUSED ? 0 : static_cast<size_t>(p.tile) * P::RB;
+    // the ring holds predicted records (cp.async), or with fused prediction
+    // the sources' double-single cache words (bulk copies)
+    constexpr int kRaw = raw_words<P>::value;
+    const size_t ring_stride = static_cast<size_t>(p.tile) * (FUSED ? kRaw * 16 : P::RB);
     unsigned char *pbuf = smem + kStages * ring_stride;  // pair records (kPair)
     double *tot = reinterpret_cast<double *>(pbuf + (kPair ? static_cast<size_t>(p.tile) * P::RB : 0)) + tid;
+
+    // fused prediction: one completion barrier per ring stage; bit s of
+    // `phase` is the parity of stage s's next completion
+    __shared__ __align__(8) unsigned long long s_bar[kStages];
+    unsigned phase = 0u;
+    if constexpr (FUSED) {
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
+            fence_barrier_init();
+        }
+        __syncthreads();
+    }
+    // one thread arms stage t % kStages and copies tile t's cache words into it
+    auto issue = [&](int t, int64_t j0_, int64_t j1_) {
+        const int64_t tb = j0_ + static_cast<int64_t>(t) * p.tile;
+        const int cnt = (tb + p.tile < j1_) ? p.tile : static_cast<int>(j1_ - tb);
+        const unsigned bytes = static_cast<unsigned>(cnt) * kRaw * 16u;
+        unsigned long long *bar = &s_bar[t % kStages];
+        unsigned char *dst = smem + static_cast<size_t>(t % kStages) * ring_stride;
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(p.dsc + tb * kRaw);
+        fence_proxy_async_smem();
+        mbar_arm(bar, bytes);
+        for (unsigned off = 0; off < bytes; off += 32768u)
+            bulk_copy_g2s(dst + off, src + off, (bytes - off < 32768u) ? bytes - off : 32768u, bar);
+    };
 
     __shared__ int s_last;
     for (int round = 0;; ++round) {
@@ -1394,14 +1476,11 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             }
         }
 
-        // fused prediction with at most two sources of a tile per thread: the
-        // first tile's cache words are requested before the sinks are read
-        constexpr int kRaw = raw_words<P>::value;
-        float4 raw[2][kRaw];
-        const bool piped = FUSED && p.tile <= 2 * nt;
+        // fused prediction: the first tiles' cache words are requested before
+        // the sinks are read
         if constexpr (FUSED) {
-            if (piped && n_tiles > 0)
-                fetch_tile<P>(p, j0, (j0 + p.tile < j1) ? p.tile : static_cast<int>(j1 - j0), raw);
+            if (tid == 0)
+                for (int s = 0; s < kStages && s < n_tiles; ++s) issue(s, j0, j1);
         }
 
         typename P::Sink sk[IPT];
@@ -1440,19 +1519,19 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             const int tb = static_cast<int>(j0) + t * p.tile;
             const unsigned char *st;
             if constexpr (FUSED) {
-                __syncthreads();  // every thread has left the previous tile
-                const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
-                if (piped) {
-                    store_tile<P>(p, cnt, raw, pbuf, jl);
-                    __syncthreads();
-                    if (t + 1 < n_tiles) {
-                        const int64_t nb = static_cast<int64_t>(tb) + p.tile;
-                        fetch_tile<P>(p, nb, (nb + p.tile < j1) ? p.tile : static_cast<int>(j1 - nb), raw);
-                    }
-                } else {
-                    predict_tile<P>(p, tb, cnt, pbuf, jl);
-                    __syncthreads();
+                const int stage = t % kStages;
+                // the barrier of this wait also means: every thread has left the previous tile
+                if (!__syncthreads_and(mbar_wait(&s_bar[stage], (phase >> stage) & 1u))) {
+                    // the copy did not complete within the limit: report it and
+                    // wait once more (bounded); give up on the pass if that fails too
+                    if (tid == 0) atomicOr(p.err, 2u);
+                    if (!__syncthreads_and(mbar_wait(&s_bar[stage], (phase >> stage) & 1u))) return;
                 }
+                phase ^= 1u << stage;
+                const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
+                predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);
+                __syncthreads();  // pair records ready, the stage is free again
+                if (tid == 0 && t + kStages < n_tiles) issue(t + kStages, j0, j1);
                 st = pbuf;
             } else {
                 cp_async_wait<kStages - 2>();
@@ -1493,7 +1572,24 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                     nd = static_cast<double>(ac[k].bd);
                     nid = ac[k].bid;
                 }
-                merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, t, nd, nid);
+                ds q[P::NS];
+                merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, q, nd, nid);
+                if (val[k]) write_fields_ds<P>(p, ii[k], slice, q, jl, lj);
+                if (P::kNN && lj == 0 && val[k]) {
+                    if (p.split == 1) {
+                        if (p.nn_id) p.nn_id[ii[k]] = nid;
+                        if (p.nn_r2) p.nn_r2[ii[k]] = (nid < 0) ? d_inf() : nd;
+                    } else if (p.sink_major) {
+                        constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+                        p.part[(ii[k] * NF + P::NS) * p.split + slice] = nd;
+                        p.part_id[ii[k] * p.split + slice] = nid;
+                    } else {
+                        const int64_t stride = static_cast<int64_t>(p.split) * p.n_i;
+                        p.part[P::NS * stride + static_cast<int64_t>(slice) * p.n_i + ii[k]] = nd;
+                        p.part_id[static_cast<int64_t>(slice) * p.n_i + ii[k]] = nid;
+                    }
+                }
+                continue;
             } else {
                 P::nn(ac[k], sk[k], p.rec, p.j_end, jl, nd, nid);
                 P::totals(ac[k], tot + k * P::NS * nt, nt, t);
@@ -1794,17 +1890,17 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // Instantiation helpers for one (order, precision) translation unit.
 // ---------------------------------------------------------------------------
 // Dynamic shared memory of a pass launch with tile records per stage: the
-// record ring (none with fused prediction), one tile of pair records (paired
+// record ring (cache words with fused prediction), one tile of pair records (paired
 // policies) and, for the mixed policies, the totals of every (thread, sink,
 // field).  The launch and occupancy helpers take the tile, not bytes.
 template <class P, int IPT, bool FUSED>
 inline size_t pass_smem(size_t tile, int threads) {
-    const size_t ring = FUSED ? 0 : kStages * tile * P::RB;
+    const size_t ring = kStages * tile * (FUSED ? raw_words<P>::value * 16 : P::RB);
     const size_t pair_bytes = is_paired<P>::value ? tile * P::RB : 0;
     return ring + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
 }
 
-constexpr int kMaxDynSmem = 200 * 1024;
+constexpr int kMaxDynSmem = kMaxPassSmem;
 
 template <class P, int IPT, bool FUSED, bool DEVN = false>
 inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t tile, cudaStream_t s) {

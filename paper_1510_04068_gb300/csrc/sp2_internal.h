@@ -60,7 +60,7 @@ struct ForceParams {
     unsigned int *queue;       // work-queue counter, zero at launch
     unsigned int *exit_count;  // if set: CTAs count out and the last resets queue and exit_count to zero
     int static_items;          // grid == n_items: CTA b takes item b and the queue is not used
-    unsigned int *err;         // set to 1 when a sink slot is outside [0, n_loaded)
+    unsigned int *err;         // bit 1: a sink slot was outside [0, n_loaded); bit 2: a bulk-copy wait gave up
     int64_t n_loaded;
     double eps2;
     // final outputs (split == 1); any may be null
@@ -123,6 +123,10 @@ struct BatchParams {
 };
 
 enum Kind { K_FORCE = 0, K_VJP = 1 };
+
+// Dynamic shared memory a pass launch may use (the 227 KiB per block of the
+// GPU, less room for the kernels' static shared variables).
+constexpr int kMaxPassSmem = 226 * 1024;
 
 // From this many slices on, the split-j reduction runs one warp per sink on
 // the sink-major partial layout (ForceParams::sink_major).
