@@ -22,7 +22,8 @@ namespace {
 
 enum Stage { ST_PREDICT = 0, ST_FORCE, ST_REDUCE, ST_BATCHED, ST_VJP, ST_OTHER, ST_COUNT };
 constexpr int kEventRing = 4096;
-constexpr int kStagesDevice = 3;  // must equal sp2::kStages of sp2_device.cuh
+constexpr int kStagesDevice = 3;       // must equal sp2::kStages of sp2_device.cuh
+constexpr int kFusedStagesDevice = 2;  // must equal sp2::kFusedStages of sp2_device.cuh
 // largest (sinks of one i-block) x (slices) reduced inside the pass kernel
 constexpr int64_t kFusedReduceMaxValues = 16384;
 
@@ -272,7 +273,8 @@ struct PassOut {
 // pair records, and for the mixed policies the 8-byte running totals of every
 // (thread, sink, field).
 size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
-    const size_t ring = static_cast<size_t>(kStagesDevice) * tile * (fused ? 16 * dscache_words(order) : rb);
+    const size_t ring = fused ? static_cast<size_t>(kFusedStagesDevice) * tile * 16 * dscache_words(order)
+                              : static_cast<size_t>(kStagesDevice) * tile * rb;
     const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
     const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
     return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);

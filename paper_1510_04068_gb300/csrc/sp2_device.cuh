@@ -19,7 +19,8 @@
 
 namespace sp2 {
 
-constexpr int kStages = 3;          // shared-memory pipeline depth
+constexpr int kStages = 3;          // shared-memory pipeline depth (cp.async ring of records)
+constexpr int kFusedStages = 2;     // bulk-copy ring of cache words (fused prediction)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxThreads = 256;
 
@@ -1416,29 +1417,30 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     // the ring holds predicted records (cp.async), or with fused prediction
     // the sources' double-single cache words (bulk copies)
     constexpr int kRaw = raw_words<P>::value;
+    constexpr int kRing = FUSED ? kFusedStages : kStages;
     const size_t ring_stride = static_cast<size_t>(p.tile) * (FUSED ? kRaw * 16 : P::RB);
-    unsigned char *pbuf = smem + kStages * ring_stride;  // pair records (kPair)
+    unsigned char *pbuf = smem + kRing * ring_stride;  // pair records (kPair)
     double *tot = reinterpret_cast<double *>(pbuf + (kPair ? static_cast<size_t>(p.tile) * P::RB : 0)) + tid;
 
     // fused prediction: one completion barrier per ring stage; bit s of
     // `phase` is the parity of stage s's next completion
-    __shared__ __align__(8) unsigned long long s_bar[kStages];
+    __shared__ __align__(8) unsigned long long s_bar[kFusedStages];
     unsigned phase = 0u;
     if constexpr (FUSED) {
         if (tid == 0) {
 #pragma unroll
-            for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
+            for (int s = 0; s < kFusedStages; ++s) mbar_init(&s_bar[s], 1u);
             fence_barrier_init();
         }
         __syncthreads();
     }
-    // one thread arms stage t % kStages and copies tile t's cache words into it
+    // one thread arms stage t % kFusedStages and copies tile t's cache words into it
     auto issue = [&](int t, int64_t j0_, int64_t j1_) {
         const int64_t tb = j0_ + static_cast<int64_t>(t) * p.tile;
         const int cnt = (tb + p.tile < j1_) ? p.tile : static_cast<int>(j1_ - tb);
         const unsigned bytes = static_cast<unsigned>(cnt) * kRaw * 16u;
-        unsigned long long *bar = &s_bar[t % kStages];
-        unsigned char *dst = smem + static_cast<size_t>(t % kStages) * ring_stride;
+        unsigned long long *bar = &s_bar[t % kFusedStages];
+        unsigned char *dst = smem + static_cast<size_t>(t % kFusedStages) * ring_stride;
         const unsigned char *src = reinterpret_cast<const unsigned char *>(p.dsc + tb * kRaw);
         fence_proxy_async_smem();
         mbar_arm(bar, bytes);
@@ -1480,7 +1482,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
         // the sinks are read
         if constexpr (FUSED) {
             if (tid == 0)
-                for (int s = 0; s < kStages && s < n_tiles; ++s) issue(s, j0, j1);
+                for (int s = 0; s < kFusedStages && s < n_tiles; ++s) issue(s, j0, j1);
         }
 
         typename P::Sink sk[IPT];
@@ -1519,7 +1521,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             const int tb = static_cast<int>(j0) + t * p.tile;
             const unsigned char *st;
             if constexpr (FUSED) {
-                const int stage = t % kStages;
+                const int stage = t % kFusedStages;
                 // the barrier of this wait also means: every thread has left the previous tile
                 if (!__syncthreads_and(mbar_wait(&s_bar[stage], (phase >> stage) & 1u))) {
                     // the copy did not complete within the limit: report it and
@@ -1531,7 +1533,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
                 predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);
                 __syncthreads();  // pair records ready, the stage is free again
-                if (tid == 0 && t + kStages < n_tiles) issue(t + kStages, j0, j1);
+                if (tid == 0 && t + kFusedStages < n_tiles) issue(t + kFusedStages, j0, j1);
                 st = pbuf;
             } else {
                 cp_async_wait<kStages - 2>();
@@ -1895,7 +1897,7 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // field).  The launch and occupancy helpers take the tile, not bytes.
 template <class P, int IPT, bool FUSED>
 inline size_t pass_smem(size_t tile, int threads) {
-    const size_t ring = kStages * tile * (FUSED ? raw_words<P>::value * 16 : P::RB);
+    const size_t ring = FUSED ? kFusedStages * tile * raw_words<P>::value * 16 : kStages * tile * P::RB;
     const size_t pair_bytes = is_paired<P>::value ? tile * P::RB : 0;
     return ring + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
 }
