@@ -272,8 +272,9 @@ struct PassOut {
 // prediction is fused: the pass predicts each tile in shared memory), for the mixed force passes one tile of
 // pair records, and for the mixed policies the 8-byte running totals of every
 // (thread, sink, field).
-size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0) {
-    const size_t ring = fused ? static_cast<size_t>(kFusedStagesDevice) * tile * 16 * dscache_words(order)
+size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int threads, int ipt, int fused = 0,
+                       int fused_stages = kFusedStagesDevice) {
+    const size_t ring = fused ? static_cast<size_t>(fused_stages) * tile * 16 * dscache_words(order)
                               : static_cast<size_t>(kStagesDevice) * tile * rb;
     const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
     const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
@@ -316,7 +317,15 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     int64_t slice_len = ceil_div(ceil_div(n_j, split), tile) * tile;
     split = ceil_div(n_j, slice_len);
     const int ns_fields = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
-    const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused);
+    // fused: two bulk-copy stages when they fit and a slice spans several
+    // tiles, else one (the next tile's copy then starts after this one's
+    // prediction)
+    const bool two_fit = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, 1, 2) <=
+                         static_cast<size_t>(kMaxPassSmem);
+    const int fused_stages = (fused && (slice_len <= tile || !two_fit)) ? 1 : kFusedStagesDevice;
+    key.fused_stages = fused ? fused_stages : 0;
+    const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused,
+                                              fused_stages);
     if (smem_total > static_cast<size_t>(kMaxPassSmem))
         return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max %d)", smem_total,
                     kMaxPassSmem);
@@ -364,6 +373,7 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         SP2_CK(c, cudaMemsetAsync(o.nb_count, 0, static_cast<size_t>(n_i) * sizeof(int32_t), c->stream));
     }
     if (fused) {
+        p.fused_stages = fused_stages;
         p.dsc = c->js.dsc;
         p.t_hi = static_cast<float>(c->t_pred);
         p.t_lo = static_cast<float>(c->t_pred - static_cast<double>(p.t_hi));
@@ -1408,8 +1418,12 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         // the kernel run_pass will launch: fused prediction when the sinks fit one i-block
         const int fused = (mixed && c->js.dsc && n_i <= int64_t(L.threads / L.j_lanes) * L.i_per_thread) ? 1 : 0;
         KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread, fused};
-        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, fused) >
-                static_cast<size_t>(kMaxPassSmem) ||
+        // a fused pass that cannot hold two bulk-copy stages runs with one
+        if (fused && pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, 1, 2) >
+                         static_cast<size_t>(kMaxPassSmem))
+            key.fused_stages = 1;
+        if (pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, fused,
+                            key.fused_stages ? key.fused_stages : 2) > static_cast<size_t>(kMaxPassSmem) ||
             force_kernel_occupancy(key, L.threads, L.j_tile, &occ) != cudaSuccess) {
             cudaGetLastError();
             return 0;
@@ -1440,7 +1454,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
                 const int64_t spc = int64_t(threads / jl) * ipt;
                 if (spc > 2 * std::max<int64_t>(n_i, 32) && threads > 32) continue;   // mostly empty CTAs
                 if (jl > 1 && spc < 8 && n_i > 4096) continue;                       // j-lanes only help few sinks
-                for (int tile : {64, 128, 256, 512}) {
+                for (int tile : {64, 128, 256, 512, 1024}) {
                     if (tile < 8 * jl) continue;
                     sp2_launch L{threads, ipt, jl, tile, 1, 0};
                     const int occ = occupancy(L);

@@ -20,7 +20,7 @@
 namespace sp2 {
 
 constexpr int kStages = 3;          // shared-memory pipeline depth (cp.async ring of records)
-constexpr int kFusedStages = 2;     // bulk-copy ring of cache words (fused prediction)
+constexpr int kFusedStages = 2;     // bulk-copy ring of cache words (fused prediction), at most
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxThreads = 256;
 
@@ -1096,6 +1096,7 @@ template <class P>
 __device__ __forceinline__ void predict_staged_tile(const ForceParams &p, const float4 *raw, int cnt,
                                                     unsigned char *q, int jl) {
     constexpr int RW = P::kRawWords;
+#pragma unroll 2
     for (int c = threadIdx.x; c < p.tile; c += blockDim.x) {
         typename P::Rec r;
         if (c < cnt) {
@@ -1417,9 +1418,10 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     // the ring holds predicted records (cp.async), or with fused prediction
     // the sources' double-single cache words (bulk copies)
     constexpr int kRaw = raw_words<P>::value;
-    constexpr int kRing = FUSED ? kFusedStages : kStages;
+    // fused: one stage when a slice fits one tile, else two
+    const int nstage = FUSED ? p.fused_stages : kStages;
     const size_t ring_stride = static_cast<size_t>(p.tile) * (FUSED ? kRaw * 16 : P::RB);
-    unsigned char *pbuf = smem + kRing * ring_stride;  // pair records (kPair)
+    unsigned char *pbuf = smem + nstage * ring_stride;  // pair records (kPair)
     double *tot = reinterpret_cast<double *>(pbuf + (kPair ? static_cast<size_t>(p.tile) * P::RB : 0)) + tid;
 
     // fused prediction: one completion barrier per ring stage; bit s of
@@ -1429,18 +1431,18 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     if constexpr (FUSED) {
         if (tid == 0) {
 #pragma unroll
-            for (int s = 0; s < kFusedStages; ++s) mbar_init(&s_bar[s], 1u);
+            for (int s = 0; s < kFusedStages; ++s) mbar_init(&s_bar[s], 1u);  // (unused stages stay idle)
             fence_barrier_init();
         }
         __syncthreads();
     }
-    // one thread arms stage t % kFusedStages and copies tile t's cache words into it
+    // one thread arms stage t % nstage and copies tile t's cache words into it
     auto issue = [&](int t, int64_t j0_, int64_t j1_) {
         const int64_t tb = j0_ + static_cast<int64_t>(t) * p.tile;
         const int cnt = (tb + p.tile < j1_) ? p.tile : static_cast<int>(j1_ - tb);
         const unsigned bytes = static_cast<unsigned>(cnt) * kRaw * 16u;
-        unsigned long long *bar = &s_bar[t % kFusedStages];
-        unsigned char *dst = smem + static_cast<size_t>(t % kFusedStages) * ring_stride;
+        unsigned long long *bar = &s_bar[t % nstage];
+        unsigned char *dst = smem + static_cast<size_t>(t % nstage) * ring_stride;
         const unsigned char *src = reinterpret_cast<const unsigned char *>(p.dsc + tb * kRaw);
         fence_proxy_async_smem();
         mbar_arm(bar, bytes);
@@ -1482,7 +1484,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
         // the sinks are read
         if constexpr (FUSED) {
             if (tid == 0)
-                for (int s = 0; s < kFusedStages && s < n_tiles; ++s) issue(s, j0, j1);
+                for (int s = 0; s < nstage && s < n_tiles; ++s) issue(s, j0, j1);
         }
 
         typename P::Sink sk[IPT];
@@ -1516,12 +1518,16 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             P::init(ac[k]);
             P::zero_totals(tot + k * P::NS * nt, nt);
         }
+        bool any_val = false;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) any_val |= val[k];
+        const bool warp_busy = __any_sync(kFull, any_val);
         int since_flush = 0;
         for (int t = 0; t < n_tiles; ++t) {
             const int tb = static_cast<int>(j0) + t * p.tile;
             const unsigned char *st;
             if constexpr (FUSED) {
-                const int stage = t % kFusedStages;
+                const int stage = t % nstage;
                 // the barrier of this wait also means: every thread has left the previous tile
                 if (!__syncthreads_and(mbar_wait(&s_bar[stage], (phase >> stage) & 1u))) {
                     // the copy did not complete within the limit: report it and
@@ -1533,7 +1539,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
                 predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);
                 __syncthreads();  // pair records ready, the stage is free again
-                if (tid == 0 && t + kFusedStages < n_tiles) issue(t + kFusedStages, j0, j1);
+                if (tid == 0 && t + nstage < n_tiles) issue(t + nstage, j0, j1);
                 st = pbuf;
             } else {
                 cp_async_wait<kStages - 2>();
@@ -1552,8 +1558,12 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             bool mine = false;
 #pragma unroll
             for (int k = 0; k < IPT; ++k) mine |= (sk[k].slot >= tb) && (sk[k].slot < te);
-            if (__any_sync(kFull, mine)) tile_loop<P, IPT, true>(st, tb, per, jl, lj, sk, ac, eps2);
-            else tile_loop<P, IPT, false>(st, tb, per, jl, lj, sk, ac, eps2);
+            // a warp whose sink slots are all empty (fewer sinks than the CTA
+            // holds) skips the tile and leaves the issue slots to the others
+            if (warp_busy) {
+                if (__any_sync(kFull, mine)) tile_loop<P, IPT, true>(st, tb, per, jl, lj, sk, ac, eps2);
+                else tile_loop<P, IPT, false>(st, tb, per, jl, lj, sk, ac, eps2);
+            }
             since_flush += per;
             if (since_flush >= P::kFlush) {
 #pragma unroll
@@ -1574,6 +1584,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                     nd = static_cast<double>(ac[k].bd);
                     nid = ac[k].bid;
                 }
+                if (!warp_busy) continue;  // no sink of this warp: nothing to merge or write
                 ds q[P::NS];
                 merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, q, nd, nid);
                 if (val[k]) write_fields_ds<P>(p, ii[k], slice, q, jl, lj);
@@ -1896,8 +1907,8 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchParams 
 // policies) and, for the mixed policies, the totals of every (thread, sink,
 // field).  The launch and occupancy helpers take the tile, not bytes.
 template <class P, int IPT, bool FUSED>
-inline size_t pass_smem(size_t tile, int threads) {
-    const size_t ring = FUSED ? kFusedStages * tile * raw_words<P>::value * 16 : kStages * tile * P::RB;
+inline size_t pass_smem(size_t tile, int threads, int fused_stages = kFusedStages) {
+    const size_t ring = FUSED ? fused_stages * tile * raw_words<P>::value * 16 : kStages * tile * P::RB;
     const size_t pair_bytes = is_paired<P>::value ? tile * P::RB : 0;
     return ring + pair_bytes + (P::kSmemTotals ? static_cast<size_t>(threads) * IPT * P::NS * sizeof(double) : 0);
 }
@@ -1907,7 +1918,7 @@ constexpr int kMaxDynSmem = kMaxPassSmem;
 template <class P, int IPT, bool FUSED, bool DEVN = false>
 inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t tile, cudaStream_t s) {
     static bool attr_set = false;
-    const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads);
+    const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads, p.fused_stages);
     if (smem > static_cast<size_t>(kMaxDynSmem)) return cudaErrorInvalidConfiguration;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel<P, IPT, FUSED, DEVN>,
@@ -1920,8 +1931,8 @@ inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size
 }
 
 template <class P, int IPT, bool FUSED, bool DEVN = false>
-inline cudaError_t occupancy_pass(int threads, size_t tile, int *blocks) {
-    const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads);
+inline cudaError_t occupancy_pass(int threads, size_t tile, int *blocks, int fused_stages = 0) {
+    const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads, fused_stages > 0 ? fused_stages : kFusedStages);
     if (smem > static_cast<size_t>(kMaxDynSmem)) {
         *blocks = 0;
         return cudaSuccess;
@@ -1947,11 +1958,11 @@ struct takes_device_count<Fp64Force<6, false>> { static constexpr bool value = t
 
 template <class P, bool FUSED>
 inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                                  cudaStream_t s, int *blocks) {
+                                  cudaStream_t s, int *blocks, int fstages = 0) {
     switch (ipt) {
-        case 1: return occ ? occupancy_pass<P, 1, FUSED>(threads, tile, blocks) : launch_pass<P, 1, FUSED>(*p, grid, threads, tile, s);
-        case 2: return occ ? occupancy_pass<P, 2, FUSED>(threads, tile, blocks) : launch_pass<P, 2, FUSED>(*p, grid, threads, tile, s);
-        case 4: return occ ? occupancy_pass<P, 4, FUSED>(threads, tile, blocks) : launch_pass<P, 4, FUSED>(*p, grid, threads, tile, s);
+        case 1: return occ ? occupancy_pass<P, 1, FUSED>(threads, tile, blocks, fstages) : launch_pass<P, 1, FUSED>(*p, grid, threads, tile, s);
+        case 2: return occ ? occupancy_pass<P, 2, FUSED>(threads, tile, blocks, fstages) : launch_pass<P, 2, FUSED>(*p, grid, threads, tile, s);
+        case 4: return occ ? occupancy_pass<P, 4, FUSED>(threads, tile, blocks, fstages) : launch_pass<P, 4, FUSED>(*p, grid, threads, tile, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1959,7 +1970,7 @@ inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int g
 // fused = 1 is available for the mixed force policies only
 template <class P>
 inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                                cudaStream_t s, int *blocks, int fused = 0, int devn = 0) {
+                                cudaStream_t s, int *blocks, int fused = 0, int devn = 0, int fstages = 0) {
     if constexpr (takes_device_count<P>::value) {
         if (devn) {
             if (ipt != 1 || fused) return cudaErrorInvalidValue;
@@ -1970,7 +1981,7 @@ inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int gri
         if (devn) return cudaErrorInvalidValue;
     }
     if constexpr (P::kCanFuse && is_paired<P>::value) {
-        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, tile, s, blocks);
+        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, tile, s, blocks, fstages);
     } else {
         if (fused) return cudaErrorInvalidValue;
     }
@@ -1980,10 +1991,10 @@ inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int gri
 // Neighbour-list kernels exist for one sink per thread only.
 template <class P>
 inline cudaError_t dispatch_nb(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                               cudaStream_t s, int *blocks, int fused) {
+                               cudaStream_t s, int *blocks, int fused, int fstages = 0) {
     if (ipt != 1) return cudaErrorInvalidValue;
     if constexpr (P::kCanFuse && is_paired<P>::value) {
-        if (fused) return occ ? occupancy_pass<P, 1, true>(threads, tile, blocks) : launch_pass<P, 1, true>(*p, grid, threads, tile, s);
+        if (fused) return occ ? occupancy_pass<P, 1, true>(threads, tile, blocks, fstages) : launch_pass<P, 1, true>(*p, grid, threads, tile, s);
     } else {
         if (fused) return cudaErrorInvalidValue;
     }
@@ -2041,12 +2052,13 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
     cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t tile, int *blocks) {       \
         if (k.nb)                                                                                          \
             return k.nn ? dispatch_nb<WithNeighbours<POLICY<ORDER, true>>>(true, k.ipt, nullptr, 0, threads, \
-                                                                           tile, 0, blocks, k.fused)       \
+                                                                           tile, 0, blocks, k.fused,        \
+                                                                           k.fused_stages)                  \
                         : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks,  \
-                                                        k.fused, k.devn)                                   \
+                                                        k.fused, k.devn, k.fused_stages)                   \
                     : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks, \
-                                                         k.fused, k.devn);                                 \
+                                                         k.fused, k.devn, k.fused_stages);                 \
     }                                                                                                      \
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {        \
         return k.nn ? launch_reduce<POLICY<ORDER, true>>(r, s) : launch_reduce<POLICY<ORDER, false>>(r, s); \

@@ -96,6 +96,7 @@ struct ForceParams {
     // the double-single cache to t = t_hi + t_lo inside the pass
     const float4 *dsc;
     float t_hi, t_lo;
+    int fused_stages;          // bulk-copy stages of the fused prediction: 1 (a slice fits one tile) or 2
 };
 
 struct ReduceParams {
@@ -143,6 +144,7 @@ struct KernelKey {
     int fused;  // 1: predict sources in the pass (mixed force only)
     int nb;     // 1: neighbour lists (force kernels with nearest neighbour, ipt 1)
     int devn;   // 1: sink count read on the device, shape derived from it (order 4 or 6, no NN, ipt 1)
+    int fused_stages;  // fused: bulk-copy stages the launch uses (0: the maximum), for the occupancy query
 };
 
 // Each kernel translation unit provides these for its (order, precision).
