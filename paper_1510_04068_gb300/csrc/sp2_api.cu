@@ -276,7 +276,7 @@ size_t pass_smem_bytes(int kind, int order, int mixed, int tile, int rb, int thr
                        int fused_stages = kFusedStagesDevice) {
     const size_t ring = fused ? static_cast<size_t>(fused_stages) * tile * 16 * dscache_words(order)
                               : static_cast<size_t>(kStagesDevice) * tile * rb;
-    const size_t pairs = (kind == K_FORCE && mixed) ? static_cast<size_t>(tile) * rb : 0;
+    const size_t pairs = mixed ? static_cast<size_t>(tile) * rb : 0;  // both mixed policies evaluate source pairs
     const int ns = (kind == K_VJP) ? 7 : (order == 6 ? 10 : (order == 2 ? 4 : 7));
     return ring + pairs + (mixed ? static_cast<size_t>(threads) * ipt * ns * 8 : 0);
 }

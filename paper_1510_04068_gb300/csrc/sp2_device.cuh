@@ -598,6 +598,18 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
         for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(t2[f * stride].x) + static_cast<double>(t2[f * stride].y);
         t[NS - 1] = -t[NS - 1];
     }
+    // the potential field is summed as +m/r and leaves with its sign changed
+    static constexpr bool kNegLast = true;
+    // summed field f of sink i into the final outputs: 0-2 acc, 3-5 jerk,
+    // 6-8 snap (order 6), NS-1 pot (null outputs are not written)
+    __device__ static __forceinline__ void store_final(const ForceParams &o, int64_t i, int f, double v) {
+        double *dst;
+        if (f == NS - 1) dst = o.pot ? o.pot + i : nullptr;
+        else if (f < 3) dst = o.acc ? o.acc + 3 * i + f : nullptr;
+        else if (f < 6) dst = o.jerk ? o.jerk + 3 * i + (f - 3) : nullptr;
+        else dst = o.snap ? o.snap + 3 * i + (f - 6) : nullptr;
+        if (dst) *dst = v;
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -945,6 +957,147 @@ struct MixedVjp {
     }
 };
 
+// ---------------------------------------------------------------------------
+// The mixed adjoint evaluated two sources at a time in packed FP32 pairs
+// (f32x2), as MixedPairForce does for the forces: the staged tile is re-laid
+// as pair records (natural word w = {e0,e1,e2,e3} of sources a and b becomes
+// {e0a,e0b,e1a,e1b}, {e2a,e2b,e3a,e3b}), the sink's values are held in both
+// halves, and each half keeps its own two-level FP32 partial sums; the halves
+// are added when the second level goes into the double-single running totals.
+// The terms are those of MixedVjp::interact (the gradients listed above).
+// ---------------------------------------------------------------------------
+struct MixedPairVjp : MixedVjp {
+    static constexpr bool kPaired = true;
+    static constexpr int PRB = 2 * RB;  // bytes of one pair record
+    struct PRec {
+        float4 w0, w1, w2, w3, w4, w6, w8;  // {xh}{yh} {zh}{m} {xl}{yl} {zl}{pbar} {vx}{vy} {abx}{aby} {jbx}{jby}
+        float2 w5, w7, w9;                  // {vz} {abz} {jbz}
+    };
+    __device__ static __forceinline__ PRec ld_pair(const unsigned char *q) {
+        const float4 *w = reinterpret_cast<const float4 *>(q);
+        PRec r;
+        r.w0 = w[0]; r.w1 = w[1]; r.w2 = w[2]; r.w3 = w[3]; r.w4 = w[4]; r.w6 = w[6]; r.w8 = w[8];
+        r.w5 = *reinterpret_cast<const float2 *>(w + 5);
+        r.w7 = *reinterpret_cast<const float2 *>(w + 7);
+        r.w9 = *reinterpret_cast<const float2 *>(w + 9);
+        return r;
+    }
+    __device__ static __forceinline__ void store_pair_word(const float4 &x, const float4 &y, int w, unsigned char *q) {
+        float4 *d = reinterpret_cast<float4 *>(q) + 2 * w;
+        d[0] = make_float4(x.x, y.x, x.y, y.y);
+        d[1] = make_float4(x.z, y.z, x.w, y.w);
+    }
+    __device__ static __forceinline__ void pack_word(const unsigned char *a, const unsigned char *b, int w,
+                                                     unsigned char *q) {
+        store_pair_word(reinterpret_cast<const float4 *>(a)[w], reinterpret_cast<const float4 *>(b)[w], w, q);
+    }
+    struct Sink {
+        float2 xh, yh, zh, xl, yl, zl, vx, vy, vz, abx, aby, abz, jbx, jby, jbz, pb, m;
+        int slot;
+    };
+    struct Acc {
+        float2 f[NS];  // level 1: xbar (3), vbar (3), mbar over the current chunk
+        float2 g[NS];  // level 2
+    };
+    __device__ static __forceinline__ void load_sink(const unsigned char *rec, int64_t slot, Sink &s) {
+        const Rec r = ld_global(rec + slot * RB);
+        s.xh = dup2(r.w[0].x); s.yh = dup2(r.w[0].y); s.zh = dup2(r.w[0].z); s.m = dup2(r.w[0].w);
+        s.xl = dup2(r.w[1].x); s.yl = dup2(r.w[1].y); s.zl = dup2(r.w[1].z); s.pb = dup2(r.w[1].w);
+        s.vx = dup2(r.w[2].x); s.vy = dup2(r.w[2].y); s.vz = dup2(r.w[2].z);
+        s.abx = dup2(r.w[3].x); s.aby = dup2(r.w[3].y); s.abz = dup2(r.w[3].z);
+        s.jbx = dup2(r.w[4].x); s.jby = dup2(r.w[4].y); s.jbz = dup2(r.w[4].z);
+    }
+    __device__ static __forceinline__ void init(Acc &c) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.f[f] = c.g[f] = dup2(0.f);
+    }
+    // Sources a (slot j) and b (slot j + jl) of the pair record r.
+    template <bool SELF, bool FIRST>
+    __device__ static __forceinline__ float2 interact2(const PRec &r, int j, int jl, int, const Sink &s, Acc &c,
+                                                       float eps2) {
+        const float2 dx = add2(sub2(make_float2(r.w0.x, r.w0.y), s.xh), sub2(make_float2(r.w2.x, r.w2.y), s.xl));
+        const float2 dy = add2(sub2(make_float2(r.w0.z, r.w0.w), s.yh), sub2(make_float2(r.w2.z, r.w2.w), s.yl));
+        const float2 dz = add2(sub2(make_float2(r.w1.x, r.w1.y), s.zh), sub2(make_float2(r.w3.x, r.w3.y), s.zl));
+        const float2 vx = sub2(make_float2(r.w4.x, r.w4.y), s.vx);
+        const float2 vy = sub2(make_float2(r.w4.z, r.w4.w), s.vy);
+        const float2 vz = sub2(r.w5, s.vz);
+        const float2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float2 d2e = add2(d2, dup2(eps2));
+        float2 rinv = make_float2(rsqrtf(d2e.x), rsqrtf(d2e.y));
+        if (SELF) {
+            if (j == s.slot) rinv.x = 0.f;
+            if (j + jl == s.slot) rinv.y = 0.f;
+        }
+        const float2 s2 = mul2(rinv, rinv), s3 = mul2(rinv, s2);
+        const float2 al = mul2(fma2(dz, vz, fma2(dy, vy, mul2(dx, vx))), s2);
+        const float2 ml = make_float2(r.w1.z, r.w1.w), pl = make_float2(r.w3.z, r.w3.w);
+        const float2 abx = make_float2(r.w6.x, r.w6.y), aby = make_float2(r.w6.z, r.w6.w), abz = r.w7;
+        const float2 jbx = make_float2(r.w8.x, r.w8.y), jby = make_float2(r.w8.z, r.w8.w), jbz = r.w9;
+        const float2 n3al = mul2(dup2(-3.f), al);
+        // sink-side sums (cotangents of the sink) and source-side sums (of the source)
+        const float2 jr1 = fma2(s.jbz, dz, fma2(s.jby, dy, mul2(s.jbx, dx)));
+        const float2 B1 = fma2(n3al, jr1, fma2(s.abz, dz, fma2(s.aby, dy, fma2(s.abx, dx,
+                                  fma2(s.jbz, vz, fma2(s.jby, vy, mul2(s.jbx, vx)))))));
+        const float2 jr2 = fma2(jbz, dz, fma2(jby, dy, mul2(jbx, dx)));
+        const float2 B2 = fma2(n3al, jr2, fma2(abz, dz, fma2(aby, dy, fma2(abx, dx,
+                                  fma2(jbz, vz, fma2(jby, vy, mul2(jbx, vx)))))));
+        const float2 q1 = mul2(ml, s3), q2 = mul2(s.m, s3);
+        const float2 D = sub2(mul2(q1, jr1), mul2(q2, jr2));
+        const float2 s2_3 = mul2(dup2(3.f), s2);
+        const float2 cv = mul2(s2_3, D);
+        // cr = 3 s^2 (q1 B1 - q2 B2) - 6 alpha s^2 D - s^3 (pbar_k m_l + pbar_l m_k)
+        const float2 ns3 = mul2(dup2(-1.f), s3);
+        const float2 cr = fma2(ns3, fma2(s.pb, ml, mul2(pl, s.m)),
+                               fma2(mul2(dup2(-2.f), al), cv, mul2(s2_3, sub2(mul2(q1, B1), mul2(q2, B2)))));
+        const float2 nq1 = mul2(dup2(-1.f), q1);
+        const float2 t1 = mul2(mul2(dup2(-1.f), n3al), q1);  // 3 alpha q1
+        const float2 nt2 = mul2(n3al, q2);                    // -3 alpha q2
+        float2 t[NS];
+        t[0] = fma2(cr, dx, fma2(cv, vx, fma2(nt2, jbx, fma2(t1, s.jbx, fma2(nq1, s.abx, mul2(q2, abx))))));
+        t[1] = fma2(cr, dy, fma2(cv, vy, fma2(nt2, jby, fma2(t1, s.jby, fma2(nq1, s.aby, mul2(q2, aby))))));
+        t[2] = fma2(cr, dz, fma2(cv, vz, fma2(nt2, jbz, fma2(t1, s.jbz, fma2(nq1, s.abz, mul2(q2, abz))))));
+        t[3] = fma2(cv, dx, fma2(nq1, s.jbx, mul2(q2, jbx)));
+        t[4] = fma2(cv, dy, fma2(nq1, s.jby, mul2(q2, jby)));
+        t[5] = fma2(cv, dz, fma2(nq1, s.jbz, mul2(q2, jbz)));
+        t[6] = fma2(ns3, B2, mul2(mul2(dup2(-1.f), pl), rinv));  // -(s^3 B2 + pbar_l s)
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.f[f] = FIRST ? t[f] : add2(c.f[f], t[f]);
+        return d2;
+    }
+    __device__ static __forceinline__ void fold(Acc &c, int, const unsigned char *, int, const Sink &) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) c.g[f] = add2(c.g[f], c.f[f]);
+    }
+    // level 2 (both halves added) -> double-single running totals, as MixedPairForce::flush
+    __device__ static __forceinline__ void flush(Acc &c, double *tot, int stride) {
+        float2 *t2 = reinterpret_cast<float2 *>(tot);
+#pragma unroll
+        for (int f = 0; f < NS; ++f) {
+            const float v = c.g[f].x + c.g[f].y;
+            float2 T = t2[f * stride];
+            const float h = T.x + v;
+            const float bv = h - T.x;
+            const float e = (T.x - (h - bv)) + (v - bv);
+            T.x = h;
+            T.y += e;
+            t2[f * stride] = T;
+            c.g[f] = dup2(0.f);
+        }
+    }
+    __device__ static __forceinline__ void zero_totals(double *tot, int stride) {
+        float2 *t2 = reinterpret_cast<float2 *>(tot);
+#pragma unroll
+        for (int f = 0; f < NS; ++f) t2[f * stride] = dup2(0.f);
+    }
+    static constexpr bool kNegLast = false;
+    // field f of particle i: 0-2 xbar, 3-5 vbar, 6 mbar (added to when accumulating)
+    __device__ static __forceinline__ void store_final(const ForceParams &o, int64_t i, int f, double v) {
+        double *dst = (f < 3) ? o.xbar + 3 * i + f : (f < 6) ? o.vbar + 3 * i + (f - 3) : o.mbar + i;
+        if (o.accumulate) *dst += v;
+        else *dst = v;
+    }
+};
+
 struct Fp64Vjp {
     static constexpr int NW = 7;
     static constexpr bool kCanFuse = false;
@@ -1201,22 +1354,13 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
     nd = static_cast<double>(d);
 }
 
-// Where summed field f of sink i goes among the final outputs (null: not
-// requested): 0-2 acc, 3-5 jerk, 6-8 snap (order 6), NS-1 pot.
-template <class P>
-__device__ __forceinline__ double *final_field(const ForceParams &o, int64_t i, int f) {
-    if (f == P::NS - 1) return o.pot ? o.pot + i : nullptr;
-    if (f < 3) return o.acc ? o.acc + 3 * i + f : nullptr;
-    if (f < 6) return o.jerk ? o.jerk + 3 * i + (f - 3) : nullptr;
-    return o.snap ? o.snap + 3 * i + (f - 6) : nullptr;
-}
-
 // A sink's merged double-single totals leave as FP64 with the fields spread
 // over its jl lanes (lane lj takes fields lj, lj + jl, ...): each lane picks
 // its field with FP32 selects, so one conversion per round serves up to jl
 // fields -- GB300 runs FP64 at 1/64 of the FP32 rate.  Field f goes to the
-// final outputs (split == 1) or to the slice's partial-sum slot; the
-// potential field changes sign (its terms were summed as +m/r).
+// final outputs (split == 1, P::store_final) or to the slice's partial-sum
+// slot; with P::kNegLast the last field changes sign (the force policies sum
+// the potential as +m/r).
 template <class P>
 __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i, int slice, const ds *q, int jl,
                                                 int lj) {
@@ -1232,12 +1376,10 @@ __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i,
             }
         if (f < P::NS) {
             double v = static_cast<double>(h) + static_cast<double>(l);
-            if (f == P::NS - 1) v = -v;
-            double *dst;
-            if (p.split == 1) dst = final_field<P>(p, i, f);
-            else if (p.sink_major) dst = p.part + (i * NF + f) * p.split + slice;
-            else dst = p.part + static_cast<int64_t>(f) * p.split * p.n_i + static_cast<int64_t>(slice) * p.n_i + i;
-            if (dst) *dst = v;
+            if (P::kNegLast && f == P::NS - 1) v = -v;
+            if (p.split == 1) P::store_final(p, i, f, v);
+            else if (p.sink_major) p.part[(i * NF + f) * p.split + slice] = v;
+            else p.part[static_cast<int64_t>(f) * p.split * p.n_i + static_cast<int64_t>(slice) * p.n_i + i] = v;
         }
     }
 }
@@ -1580,9 +1722,11 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             double nd = d_inf();
             int nid = -1;
             if constexpr (kPair) {
-                if (P::kNN && ac[k].bid >= 0) {
-                    nd = static_cast<double>(ac[k].bd);
-                    nid = ac[k].bid;
+                if constexpr (P::kNN) {
+                    if (ac[k].bid >= 0) {
+                        nd = static_cast<double>(ac[k].bd);
+                        nid = ac[k].bid;
+                    }
                 }
                 if (!warp_busy) continue;  // no sink of this warp: nothing to merge or write
                 ds q[P::NS];

@@ -1,5 +1,5 @@
 // sp2_kernels_vjp.cu -- instantiation unit of the adjoint (VJP) pass in both
-// precisions.  The VJP reuses the persistent pass skeleton and the split-j
+// precisions (mixed: the paired f32x2 policy MixedPairVjp).  The VJP reuses the persistent pass skeleton and the split-j
 // reduction; it has no batched form.
 #include "sp2_device.cuh"
 
@@ -21,7 +21,7 @@ namespace sp2 {
     }                                                                                                   \
     cudaError_t occupancy_batched_##SUFFIX(int, int, int *) { return cudaErrorInvalidValue; }
 
-SP2_VJP_TU(vjpm, MixedVjp)
+SP2_VJP_TU(vjpm, MixedPairVjp)
 SP2_VJP_TU(vjpd, Fp64Vjp)
 #undef SP2_VJP_TU
 
