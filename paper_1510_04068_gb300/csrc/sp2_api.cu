@@ -335,10 +335,30 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         SP2_CK(c, force_kernel_occupancy(key, L.threads, tile, &per_sm));
         if (per_sm <= 0) return fail(c, SP2_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
     }
-    const int64_t n_items = n_iblk * split;
     // a device-count pass may make more work items than the host's bound
     // shows: it takes every resident CTA
     const int64_t resident = static_cast<int64_t>(c->sm_count) * per_sm;
+    // At least a wave of i-blocks: whole waves of them run unsplit (one item
+    // over all sources each, outputs written directly) and only the rest is
+    // split, into as many slices as fill one wave -- the same balance as
+    // splitting everything, with partial sums for the last wave's sinks only.
+    int64_t n_whole = 0;
+    if (!devn && split > 1 && n_iblk >= resident) {
+        n_whole = n_iblk / resident * resident;
+        const int64_t rest = n_iblk - n_whole;
+        int64_t tail_split = rest > 0 ? std::min<int64_t>(resident / rest, ceil_div(n_j, tile)) : 1;
+        if (tail_split > 1 && sinks_per_cta * tail_split <= kFusedReduceMaxValues) {
+            slice_len = ceil_div(ceil_div(n_j, tail_split), tile) * tile;
+            split = ceil_div(n_j, slice_len);
+        } else {
+            n_whole = n_iblk;
+            split = 1;
+            slice_len = n_j;
+        }
+    }
+    const int64_t tail_sink0 = n_whole * sinks_per_cta;
+    const int64_t n_part = n_i - tail_sink0;  // sinks with partial rows
+    const int64_t n_items = n_whole + (n_iblk - n_whole) * split;
     const int grid = static_cast<int>(devn ? resident : std::min<int64_t>(n_items, resident));
     const int static_items = (!n_i_dev && grid == n_items) ? 1 : 0;  // one wave: CTA b takes item b
 
@@ -356,6 +376,8 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     p.sinks_per_cta = static_cast<int>(sinks_per_cta);
     p.n_iblk = n_iblk;
     p.n_items = n_items;
+    p.n_whole = n_whole;
+    p.tail_sink0 = tail_sink0;
     p.queue = c->dev_words + 4;       // self-resetting work counter of the pass kernel
     p.exit_count = c->dev_words + 5;
     p.static_items = static_items;
@@ -380,10 +402,10 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
     }
     const int ns = ns_fields;
     if (split > 1) {
-        const size_t need = static_cast<size_t>(ns + (nn ? 1 : 0)) * split * n_i * sizeof(double);
+        const size_t need = static_cast<size_t>(ns + (nn ? 1 : 0)) * split * n_part * sizeof(double);
         SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->part), &c->part_cap, need, "partial-sum"));
         if (nn) SP2_CKS(ensure(c, reinterpret_cast<void **>(&c->part_id), &c->part_id_cap,
-                               static_cast<size_t>(split) * n_i * sizeof(int32_t), "partial-id"));
+                               static_cast<size_t>(split) * n_part * sizeof(int32_t), "partial-id"));
         p.part = c->part;
         p.part_id = c->part_id;
         p.sink_major = split >= kWarpReduceMinSplit ? 1 : 0;

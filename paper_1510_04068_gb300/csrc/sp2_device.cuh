@@ -1361,9 +1361,11 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
 // final outputs (split == 1, P::store_final) or to the slice's partial-sum
 // slot; with P::kNegLast the last field changes sign (the force policies sum
 // the potential as +m/r).
+// split == 1: final outputs of sink i; else the partial-sum slot of the
+// slice for partial row pi of pn (the sinks that have partials).
 template <class P>
-__device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i, int slice, const ds *q, int jl,
-                                                int lj) {
+__device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i, int split, int slice, int64_t pi,
+                                                int64_t pn, const ds *q, int jl, int lj) {
     constexpr int NF = P::NS + (P::kNN ? 1 : 0);
     for (int f0 = 0; f0 < P::NS; f0 += jl) {
         const int f = f0 + lj;
@@ -1377,9 +1379,9 @@ __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i,
         if (f < P::NS) {
             double v = static_cast<double>(h) + static_cast<double>(l);
             if (P::kNegLast && f == P::NS - 1) v = -v;
-            if (p.split == 1) P::store_final(p, i, f, v);
-            else if (p.sink_major) p.part[(i * NF + f) * p.split + slice] = v;
-            else p.part[static_cast<int64_t>(f) * p.split * p.n_i + static_cast<int64_t>(slice) * p.n_i + i] = v;
+            if (split == 1) P::store_final(p, i, f, v);
+            else if (p.sink_major) p.part[(pi * NF + f) * split + slice] = v;
+            else p.part[static_cast<int64_t>(f) * split * pn + static_cast<int64_t>(slice) * pn + pi] = v;
         }
     }
 }
@@ -1486,8 +1488,10 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     const int64_t b0 = iblk * p.sinks_per_cta;
     const int64_t b1 = (b0 + p.sinks_per_cta < p.n_i) ? b0 + p.sinks_per_cta : p.n_i;
     const int split = p.split;
+    // partial rows are counted from the first sink of the split i-blocks
+    const int64_t r0 = p.tail_sink0, pn = p.n_i - p.tail_sink0;
     if (!p.sink_major) {
-        const int64_t stride = static_cast<int64_t>(split) * p.n_i;
+        const int64_t stride = static_cast<int64_t>(split) * pn;
         for (int64_t i = b0 + tid; i < b1; i += nt) {
             double t[P::NS];
 #pragma unroll
@@ -1495,10 +1499,10 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
             double nd = d_inf();
             int nid = -1;
             for (int s = 0; s < split; ++s) {
-                const double *base = p.part + static_cast<int64_t>(s) * p.n_i + i;
+                const double *base = p.part + static_cast<int64_t>(s) * pn + (i - r0);
 #pragma unroll
                 for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(base + f * stride);
-                if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(p.part_id + static_cast<int64_t>(s) * p.n_i + i));
+                if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(p.part_id + static_cast<int64_t>(s) * pn + (i - r0)));
             }
             P::write_final(p, i, t, nd, nid);
         }
@@ -1507,14 +1511,14 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     if (b1 - b0 < nw) {
         // few sinks: the whole CTA on each, one warp per field
         for (int64_t i = b0; i < b1; ++i)
-            reduce_sink_fields<P>(p.part + i * NF * split, p.part_id + i * split, split, s_f, s_nd, s_nid,
+            reduce_sink_fields<P>(p.part + (i - r0) * NF * split, p.part_id + (i - r0) * split, split, s_f, s_nd, s_nid,
                                   [&](const double *t, double d, int id) { P::write_final(p, i, t, d, id); });
         return;
     }
     // a warp per sink
     for (int64_t i = b0 + warp; i < b1; i += nw) {
-        const double *row = p.part + i * NF * split;
-        const int32_t *row_id = p.part_id + i * split;
+        const double *row = p.part + (i - r0) * NF * split;
+        const int32_t *row_id = p.part_id + (i - r0) * split;
         double t[P::NS];
 #pragma unroll
         for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
@@ -1606,13 +1610,28 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             item = s_item;
         }
         if (item >= p.n_items) break;
-        const int64_t iblk = item % p.n_iblk;
-        const int slice = static_cast<int>(item / p.n_iblk);
+        // items 0 .. n_whole-1: i-blocks over all sources (final outputs);
+        // then (i-block, slice) items of the remaining i-blocks (partials)
+        int64_t iblk, slen;
+        int slice, isplit;
+        if (item < p.n_whole) {
+            iblk = item;
+            slice = 0;
+            isplit = 1;
+            slen = p.j_end - p.j_begin;
+        } else {
+            const int64_t k = item - p.n_whole, n_rest = p.n_iblk - p.n_whole;
+            iblk = p.n_whole + k % n_rest;
+            slice = static_cast<int>(k / n_rest);
+            isplit = p.split;
+            slen = p.slice_len;
+        }
+        const int64_t pn = p.n_i - p.tail_sink0;  // sinks with partial rows
 
         // the slice's first tiles are requested before the sinks are read, so
         // the two memory round trips overlap
-        const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
-        const int64_t j1 = (j0 + p.slice_len < p.j_end) ? j0 + p.slice_len : p.j_end;
+        const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * slen;
+        const int64_t j1 = (j0 + slen < p.j_end) ? j0 + slen : p.j_end;
         const int n_tiles = static_cast<int>((j1 - j0 + p.tile - 1) / p.tile);
         if constexpr (!FUSED) {
 #pragma unroll
@@ -1731,19 +1750,20 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 if (!warp_busy) continue;  // no sink of this warp: nothing to merge or write
                 ds q[P::NS];
                 merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, q, nd, nid);
-                if (val[k]) write_fields_ds<P>(p, ii[k], slice, q, jl, lj);
+                const int64_t pi = ii[k] - p.tail_sink0;
+                if (val[k]) write_fields_ds<P>(p, ii[k], isplit, slice, pi, pn, q, jl, lj);
                 if (P::kNN && lj == 0 && val[k]) {
-                    if (p.split == 1) {
+                    if (isplit == 1) {
                         if (p.nn_id) p.nn_id[ii[k]] = nid;
                         if (p.nn_r2) p.nn_r2[ii[k]] = (nid < 0) ? d_inf() : nd;
                     } else if (p.sink_major) {
                         constexpr int NF = P::NS + (P::kNN ? 1 : 0);
-                        p.part[(ii[k] * NF + P::NS) * p.split + slice] = nd;
-                        p.part_id[ii[k] * p.split + slice] = nid;
+                        p.part[(pi * NF + P::NS) * isplit + slice] = nd;
+                        p.part_id[pi * isplit + slice] = nid;
                     } else {
-                        const int64_t stride = static_cast<int64_t>(p.split) * p.n_i;
-                        p.part[P::NS * stride + static_cast<int64_t>(slice) * p.n_i + ii[k]] = nd;
-                        p.part_id[static_cast<int64_t>(slice) * p.n_i + ii[k]] = nid;
+                        const int64_t stride = static_cast<int64_t>(isplit) * pn;
+                        p.part[P::NS * stride + static_cast<int64_t>(slice) * pn + pi] = nd;
+                        p.part_id[static_cast<int64_t>(slice) * pn + pi] = nid;
                     }
                 }
                 continue;
@@ -1761,30 +1781,31 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 }
             }
             if (lj == 0 && val[k]) {
-                if (p.split == 1) {
+                const int64_t pi = ii[k] - p.tail_sink0;
+                if (isplit == 1) {
                     P::write_final(p, ii[k], t, nd, nid);
                 } else if (p.sink_major) {
                     constexpr int NF = P::NS + (P::kNN ? 1 : 0);
-                    double *base = p.part + ii[k] * NF * p.split + slice;
+                    double *base = p.part + pi * NF * isplit + slice;
 #pragma unroll
-                    for (int f = 0; f < P::NS; ++f) base[f * p.split] = t[f];
+                    for (int f = 0; f < P::NS; ++f) base[f * isplit] = t[f];
                     if (P::kNN) {
-                        base[P::NS * p.split] = nd;
-                        p.part_id[ii[k] * p.split + slice] = nid;
+                        base[P::NS * isplit] = nd;
+                        p.part_id[pi * isplit + slice] = nid;
                     }
                 } else {
-                    const int64_t stride = static_cast<int64_t>(p.split) * p.n_i;
-                    double *base = p.part + static_cast<int64_t>(slice) * p.n_i + ii[k];
+                    const int64_t stride = static_cast<int64_t>(isplit) * pn;
+                    double *base = p.part + static_cast<int64_t>(slice) * pn + pi;
 #pragma unroll
                     for (int f = 0; f < P::NS; ++f) base[f * stride] = t[f];
                     if (P::kNN) {
                         base[P::NS * stride] = nd;
-                        p.part_id[static_cast<int64_t>(slice) * p.n_i + ii[k]] = nid;
+                        p.part_id[static_cast<int64_t>(slice) * pn + pi] = nid;
                     }
                 }
             }
         }
-        if (p.split > 1 && p.fused_reduce) {
+        if (isplit > 1 && p.fused_reduce) {
             // every partial of this CTA is written (barrier); thread 0's fence
             // then makes them visible device-wide before the CTA is counted
             __syncthreads();

@@ -56,7 +56,12 @@ struct ForceParams {
     int tile;                  // records per shared-memory stage
     int sinks_per_cta;         // threads / jl * ipt
     int64_t n_iblk;            // i-blocks
-    int64_t n_items;           // n_iblk * split
+    int64_t n_items;           // n_whole + (n_iblk - n_whole) * split
+    // i-blocks 0 .. n_whole-1 run over all sources as one item each and
+    // write their outputs directly; only the remaining i-blocks are split and
+    // have partial rows, counted from sink tail_sink0 = n_whole * sinks_per_cta
+    int64_t n_whole;
+    int64_t tail_sink0;
     unsigned int *queue;       // work-queue counter, zero at launch
     unsigned int *exit_count;  // if set: CTAs count out and the last resets queue and exit_count to zero
     int static_items;          // grid == n_items: CTA b takes item b and the queue is not used
@@ -67,11 +72,12 @@ struct ForceParams {
     double *acc, *jerk, *snap, *pot;
     int32_t *nn_id;
     double *nn_r2;
-    // partial results (split > 1), NF = summed fields (+1 for the NN r^2):
-    //   field-major (sink_major = 0): part[f * split * n_i + slice * n_i + i],
-    //                                 part_id[slice * n_i + i]
-    //   sink-major  (sink_major = 1): part[(i * NF + f) * split + slice],
-    //                                 part_id[i * split + slice]
+    // partial results (split > 1), NF = summed fields (+1 for the NN r^2),
+    // r = i - tail_sink0 the partial row of sink i, pn = n_i - tail_sink0:
+    //   field-major (sink_major = 0): part[f * split * pn + slice * pn + r],
+    //                                 part_id[slice * pn + r]
+    //   sink-major  (sink_major = 1): part[(r * NF + f) * split + slice],
+    //                                 part_id[r * split + slice]
     // sink-major is used with the warp-per-sink reduction (split >= 32), so a
     // warp reads its sink's slices contiguously.
     double *part;

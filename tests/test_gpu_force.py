@@ -220,3 +220,19 @@ def test_mixed_far_from_origin(sp2, oracle_mod, order):
     g = gpu_run(sp2, s, idx, order=order, precision=sp2.SP2_MIXED, eps2=eps2)
     r = oracle_ref(oracle_mod, s, idx, order=order, eps2=eps2)
     check(g, r, order=order, mixed=True, s=s, i_idx=idx, label="far from origin")
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("n,per_sm", [(12000, 1), (20000, 2)])
+def test_whole_waves_and_split_tail(sp2, oracle_mod, mixed, n, per_sm):
+    """More i-blocks than resident CTAs (one resident CTA of 32 sinks per SM
+    here): whole waves of i-blocks run over all sources and write their
+    outputs directly, the last partial wave is split over the sources and
+    reduced in the pass; every sink matches the oracle."""
+    eps2 = 1e-8
+    s = state(n, 81, order=4)
+    idx = np.random.default_rng(n).permutation(n).astype(np.int32)
+    launch = dict(threads=32, i_per_thread=1, j_lanes=1, j_tile=64, split_j=4, ctas_per_sm=per_sm)
+    g = gpu_run(sp2, s, idx, order=4, precision=sp2.SP2_MIXED if mixed else sp2.SP2_FP64, eps2=eps2, launch=launch)
+    r = oracle_ref(oracle_mod, s, idx, order=4, eps2=eps2)
+    check(g, r, order=4, mixed=mixed, s=s, i_idx=idx, label=f"n={n} per_sm={per_sm}")
