@@ -1387,7 +1387,7 @@ __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i,
 }
 
 // FP64 reduction of one sink's slices (sink-major row: field f's slices are
-// contiguous) by the whole CTA, fields spread over the warps: lane l of a
+// contiguous) by the whole CTA, fields spread over the warps (two at a time): lane l of a
 // warp sums slices l, l+32, ... of a field in order, a fixed xor-butterfly
 // combines the lanes, and the field totals meet in shared memory, where
 // thread 0 writes the outputs (write(t, d, id)).  Different warps work on
@@ -1399,30 +1399,30 @@ template <class P, class Write>
 __device__ __forceinline__ void reduce_sink_fields(const double *row, const int32_t *row_id, int split, double *s_f,
                                                    long long &s_nd, int &s_nid, const Write &write) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    // sums: warp w takes fields w, w + nw, ... four at a time with their adds
+    // sums: warp w takes fields w, w + nw, ... two at a time with their adds
     // interleaved (independent FP64 chains keep the FP64 pipe busy)
-    for (int f0 = warp; f0 < P::NS; f0 += 4 * nw) {
-        bool on[4];
-        const double *col[4];
+    for (int f0 = warp; f0 < P::NS; f0 += 2 * nw) {
+        bool on[2];
+        const double *col[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
             on[q] = f0 + q * nw < P::NS;
             col[q] = row + static_cast<int64_t>(on[q] ? f0 + q * nw : f0) * split;
         }
         // lane l adds slices l, l + 32, l + 64, ... in that order; the loads of
         // 256 slices per field are all issued before the first add
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        double v[2] = {0.0, 0.0};
         for (int s0 = 0; s0 < split; s0 += 8 * 32) {
-            double x[4][8];
+            double x[2][8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 2; ++q)
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int s = s0 + lane + 32 * e;
                     x[q][e] = (on[q] && s < split) ? __ldcg(col[q] + s) : 0.0;
                 }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 2; ++q)
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
                     if (s0 + lane + 32 * e < split) v[q] += x[q][e];
@@ -1430,10 +1430,10 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
+            for (int q = 0; q < 2; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
         if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 2; ++q)
                 if (on[q]) s_f[f0 + q * nw] = v[q];
     }
     if (P::kNN && warp == nw - 1) {
@@ -1498,11 +1498,13 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
             for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
             double nd = d_inf();
             int nid = -1;
-            for (int s = 0; s < split; ++s) {
-                const double *base = p.part + static_cast<int64_t>(s) * pn + (i - r0);
+            const double *base = p.part + (i - r0);       // slice 0, field 0 of this sink's row
+            const int32_t *base_id = p.part_id + (i - r0);
+#pragma unroll 2
+            for (int s = 0; s < split; ++s, base += pn, base_id += pn) {
 #pragma unroll
                 for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(base + f * stride);
-                if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(p.part_id + static_cast<int64_t>(s) * pn + (i - r0)));
+                if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(base_id));
             }
             P::write_final(p, i, t, nd, nid);
         }
@@ -1612,26 +1614,24 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
         if (item >= p.n_items) break;
         // items 0 .. n_whole-1: i-blocks over all sources (final outputs);
         // then (i-block, slice) items of the remaining i-blocks (partials)
-        int64_t iblk, slen;
-        int slice, isplit;
-        if (item < p.n_whole) {
+        // (work items, i-blocks and slices stay below 2^31)
+        const bool whole = item < p.n_whole;
+        int64_t iblk;
+        int slice;
+        if (whole) {
             iblk = item;
             slice = 0;
-            isplit = 1;
-            slen = p.j_end - p.j_begin;
         } else {
-            const int64_t k = item - p.n_whole, n_rest = p.n_iblk - p.n_whole;
-            iblk = p.n_whole + k % n_rest;
+            const unsigned k = static_cast<unsigned>(item - p.n_whole);
+            const unsigned n_rest = static_cast<unsigned>(p.n_iblk - p.n_whole);
+            iblk = p.n_whole + static_cast<int64_t>(k % n_rest);
             slice = static_cast<int>(k / n_rest);
-            isplit = p.split;
-            slen = p.slice_len;
         }
-        const int64_t pn = p.n_i - p.tail_sink0;  // sinks with partial rows
 
         // the slice's first tiles are requested before the sinks are read, so
         // the two memory round trips overlap
-        const int64_t j0 = p.j_begin + static_cast<int64_t>(slice) * slen;
-        const int64_t j1 = (j0 + slen < p.j_end) ? j0 + slen : p.j_end;
+        const int64_t j0 = whole ? p.j_begin : p.j_begin + static_cast<int64_t>(slice) * p.slice_len;
+        const int64_t j1 = (whole || j0 + p.slice_len >= p.j_end) ? p.j_end : j0 + p.slice_len;
         const int n_tiles = static_cast<int>((j1 - j0 + p.tile - 1) / p.tile);
         if constexpr (!FUSED) {
 #pragma unroll
@@ -1734,6 +1734,8 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
         }
         cp_async_wait<0>();
 
+        const int isplit = whole ? 1 : p.split;
+        const int64_t pn = p.n_i - p.tail_sink0;  // sinks with partial rows
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             P::flush(ac[k], tot + k * P::NS * nt, nt);
