@@ -223,9 +223,9 @@ def test_mixed_far_from_origin(sp2, oracle_mod, order):
 
 
 @pytest.mark.parametrize("mixed", [False, True])
-@pytest.mark.parametrize("n,per_sm", [(12000, 1), (20000, 2)])
+@pytest.mark.parametrize("n,per_sm", [(24000, 1), (45000, 1)])
 def test_whole_waves_and_split_tail(sp2, oracle_mod, mixed, n, per_sm):
-    """More i-blocks than resident CTAs (one resident CTA of 32 sinks per SM
+    """Four or more waves of i-blocks (one resident CTA of 32 sinks per SM
     here): whole waves of i-blocks run over all sources and write their
     outputs directly, the last partial wave is split over the sources and
     reduced in the pass; every sink matches the oracle."""
