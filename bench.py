@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--blk6-t-end", type=float, default=1.0,
                    help="end time of the 6th-order block-step runs (Sec. 3.7 integrates one N-body time unit)")
     p.add_argument("--blk6-n", default="16384", help="particle counts of the 6th-order block-step runs")
+    p.add_argument("--blk6-eps", default="1e-3", help="softening lengths of the 6th-order block-step runs")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
@@ -444,7 +445,8 @@ def run_ours(args, world, rank, local):
         line["e2e"] = e2e(ctx, w, upd, out, args, stream, j_range, world)
     if not args.no_extras and rank == 0:
         line["detail"] = extras(sp2, w, n, eps2, dev, stream, set(args.extras.split(",")), args.blk_t_end,
-                                args.blk6_t_end, tuple(int(q) for q in args.blk6_n.split(",")))
+                                args.blk6_t_end, tuple(int(q) for q in args.blk6_n.split(",")),
+                                tuple(float(q) for q in args.blk6_eps.split(",")))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -505,7 +507,8 @@ def timed(fn, reps, stream):
     return statistics.median(ts)
 
 
-def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.0, blk6_n=(16384,)):
+def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.0, blk6_n=(16384,),
+           blk6_eps=(1e-3,)):
     """N_active sweep (mixed vs FP64), batched systems, adjoint: secondary lines."""
     import torch
     D = lambda q: torch.as_tensor(np.ascontiguousarray(q)).to(dev)  # noqa: E731
@@ -528,7 +531,8 @@ def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.
         if "blk" in sections:
             res["blk"] = bench_blk(sp2, dev, stream, t_end=blk_t_end)
         if "blk6" in sections:
-            res["blk6"] = [r for nb in blk6_n for r in bench_blk6(sp2, dev, stream, n=nb, t_end=blk6_t_end)]
+            res["blk6"] = [r for nb in blk6_n for e in blk6_eps
+                           for r in bench_blk6(sp2, dev, stream, n=nb, t_end=blk6_t_end, eps=e)]
     return res
 
 
@@ -782,16 +786,16 @@ def bench_blk(sp2, dev, stream, n=16384, t_end=0.25):
     return rows
 
 
-def bench_blk6(sp2, dev, stream, n=16384, t_end=1.0):
+def bench_blk6(sp2, dev, stream, n=16384, t_end=1.0, eps=1e-3):
     """6th-order block time-steps with the averaged criterion (eta4 = 0.01,
     eta6 = 0.1, steps <= 1/16; the scheme and parameters of Sec. 3.7, one
-    N-body time unit by default) on a Plummer sphere, eps = 1e-3, mixed and
+    N-body time unit by default) on a Plummer sphere (softening eps), mixed and
     FP64: wall time, blocks, mean / min / max N_active and the relative energy
     error at t_end (energies from an FP64 context of the library), or the
     time at which a run stopped on the step-underflow guard."""
     import time
     import torch
-    eps2 = 1e-6
+    eps2 = eps * eps
     m, x, v = W.plummer(n, 21)
     ids = np.arange(n, dtype=np.int32)
     z = np.zeros((n, 3))
@@ -819,7 +823,7 @@ def bench_blk6(sp2, dev, stream, n=16384, t_end=1.0):
         except sp2.SP2Error as e:  # step underflow (the collapse Sec. 3.7 warns of for DS forces)
             torch.cuda.synchronize()
             st = getattr(e, "stats", {})
-            rows.append({"precision": name, "n": n, "t_end": t_end, "wall_s": time.perf_counter() - w0,
+            rows.append({"precision": name, "n": n, "eps": eps, "t_end": t_end, "wall_s": time.perf_counter() - w0,
                          "stopped": str(e), "stopped_at_t": st.get("t"), "block_steps": st.get("block_steps"),
                          "mean_active": st.get("active_sum", 0) / max(st.get("block_steps") or 1, 1)})
             c.close()
@@ -829,7 +833,7 @@ def bench_blk6(sp2, dev, stream, n=16384, t_end=1.0):
         xs, vs = np.empty((n, 3)), np.empty((n, 3))
         c.get_j(0, n, x=xs, v=vs)
         c.close()
-        rows.append({"precision": name, "n": n, "t_end": t_end, "wall_s": wall, "block_steps": st["block_steps"],
+        rows.append({"precision": name, "n": n, "eps": eps, "t_end": t_end, "wall_s": wall, "block_steps": st["block_steps"],
                      "mean_active": st["active_sum"] / max(st["block_steps"], 1),
                      "min_active": st["min_active"], "max_active": st["max_active"],
                      "us_per_block": 1e6 * wall / max(st["block_steps"], 1),

@@ -1622,10 +1622,13 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             iblk = item;
             slice = 0;
         } else {
+            // i-block-major: the slices of one i-block are taken one after the
+            // other, so they finish close together and its partial sums are
+            // reduced while they are still fresh in L2
             const unsigned k = static_cast<unsigned>(item - p.n_whole);
-            const unsigned n_rest = static_cast<unsigned>(p.n_iblk - p.n_whole);
-            iblk = p.n_whole + static_cast<int64_t>(k % n_rest);
-            slice = static_cast<int>(k / n_rest);
+            const unsigned sp = static_cast<unsigned>(p.split);
+            iblk = p.n_whole + static_cast<int64_t>(k / sp);
+            slice = static_cast<int>(k % sp);
         }
 
         // the slice's first tiles are requested before the sinks are read, so
