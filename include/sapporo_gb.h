@@ -88,8 +88,12 @@ typedef struct {
 typedef struct {
     int threads;       /* threads per CTA: 32, 64, 128 or 256                         */
     int i_per_thread;  /* sinks held by one thread: 1, 2 or 4                          */
-    int j_lanes;       /* threads sharing one sink, each taking every j_lanes-th source:
-                          1, 2, 4, ..., min(32, threads) (the paper's 2D blocks)  */
+    int j_lanes;       /* threads sharing one sink (the paper's 2D blocks): 1, 2, 4,
+                          ..., threads.  Up to 32 they are lanes of one warp, each
+                          taking every j_lanes-th source of a tile; above 32
+                          (SP2_MIXED, i_per_thread 1) j_lanes / 32 warps share
+                          the sink, each taking its own contiguous part of
+                          every tile                                          */
     int j_tile;        /* sources staged in shared memory per pipeline stage          */
     int split_j;       /* source slices processed independently, combined by the
                           FP64 reduction kernel (1: no reduction pass)                */

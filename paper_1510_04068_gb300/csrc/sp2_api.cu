@@ -213,8 +213,8 @@ sp2_status check_launch(sp2_ctx *c, const sp2_launch &L) {
         return fail(c, SP2_ERR_ARG, "threads must be 32, 64, 128 or 256");
     if (!(L.i_per_thread == 1 || L.i_per_thread == 2 || L.i_per_thread == 4))
         return fail(c, SP2_ERR_ARG, "i_per_thread must be 1, 2 or 4");
-    if (!pow2(L.j_lanes) || L.j_lanes > 32 || L.j_lanes > L.threads)
-        return fail(c, SP2_ERR_ARG, "j_lanes must be a power of two <= min(32, threads)");
+    if (!pow2(L.j_lanes) || L.j_lanes > L.threads)
+        return fail(c, SP2_ERR_ARG, "j_lanes must be a power of two <= threads");
     if (L.j_tile < 16 || L.j_tile > 1024 || !pow2(L.j_tile) || L.j_tile < 8 * L.j_lanes)
         return fail(c, SP2_ERR_ARG, "j_tile must be a power of two in [16, 1024] and >= 8 * j_lanes");
     if (L.split_j < 1 || L.split_j > 65536) return fail(c, SP2_ERR_ARG, "split_j must be in [1, 65536]");
@@ -330,6 +330,9 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
         return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max %d)", smem_total,
                     kMaxPassSmem);
     if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
+    if (jl > 32 && (!mixed || L.i_per_thread != 1))
+        return fail(c, SP2_ERR_UNSUPPORTED,
+                    "j_lanes above 32 (several warps per sink) need a mixed-precision context and i_per_thread 1");
     int per_sm = L.ctas_per_sm;
     if (per_sm <= 0) {
         SP2_CK(c, force_kernel_occupancy(key, L.threads, tile, &per_sm));
@@ -1475,7 +1478,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
     std::vector<std::pair<float, sp2_launch>> shapes;
     for (int threads : {64, 128, 256})
         for (int ipt : {1, 2, 4})
-            for (int jl = 1; jl <= 32; jl *= 2) {
+            for (int jl = 1; jl <= ((mixed && ipt == 1) ? threads : 32); jl *= 2) {
                 if (jl > threads) continue;
                 const int64_t spc = int64_t(threads / jl) * ipt;
                 if (spc > 2 * std::max<int64_t>(n_i, 32) && threads > 32) continue;   // mostly empty CTAs

@@ -84,6 +84,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     return false;
 }
 
+// Drop the 128-byte L2 lines that lie wholly inside [lo, hi) without writing
+// them back (their contents are not needed again); lines shared with
+// neighbouring data are kept.  Called by all threads of a CTA.
+__device__ __forceinline__ void discard_l2_range(const void *lo, const void *hi) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(lo) + 127u) & ~static_cast<uintptr_t>(127u);
+    const uintptr_t e = reinterpret_cast<uintptr_t>(hi) & ~static_cast<uintptr_t>(127u);
+    for (uintptr_t q = a + static_cast<uintptr_t>(threadIdx.x) * 128u; q < e; q += static_cast<uintptr_t>(blockDim.x) * 128u)
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(q) : "memory");
+}
+
 __device__ __forceinline__ uint4 f4bits(float a, float b, float c, float d) {
     return make_uint4(__float_as_uint(a), __float_as_uint(b), __float_as_uint(c), __float_as_uint(d));
 }
@@ -1545,6 +1555,29 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     }
 }
 
+// The partial-sum rows of one split i-block, dropped from L2 once reduced.
+template <class P>
+__device__ __forceinline__ void discard_partials(const ForceParams &p, int64_t iblk) {
+    constexpr int NF = P::NS + (P::kNN ? 1 : 0);
+    const int64_t b0 = iblk * p.sinks_per_cta - p.tail_sink0;
+    const int64_t b1 = ((iblk * p.sinks_per_cta + p.sinks_per_cta < p.n_i) ? iblk * p.sinks_per_cta + p.sinks_per_cta
+                                                                          : p.n_i) - p.tail_sink0;
+    const int64_t pn = p.n_i - p.tail_sink0;
+    const int split = p.split;
+    if (p.sink_major) {
+        discard_l2_range(p.part + b0 * NF * split, p.part + b1 * NF * split);
+        if (P::kNN) discard_l2_range(p.part_id + b0 * split, p.part_id + b1 * split);
+        return;
+    }
+    for (int f = 0; f < NF; ++f)
+        for (int sl = 0; sl < split; ++sl) {
+            const double *row = p.part + (static_cast<int64_t>(f) * split + sl) * pn;
+            discard_l2_range(row + b0, row + b1);
+        }
+    if (P::kNN)
+        for (int sl = 0; sl < split; ++sl) discard_l2_range(p.part_id + sl * pn + b0, p.part_id + sl * pn + b1);
+}
+
 // Shared memory: kStages tiles of records, (paired policies) one tile of pair
 // records, then (mixed policies) the running totals (8 bytes each: FP64, or a
 // double-single pair in the paired policy), [sink k][field f][thread]
@@ -1555,12 +1588,21 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     __shared__ unsigned int s_item;
     const int tid = threadIdx.x;
     const int nt = blockDim.x;
-    const int jl = p.jl;
+    // p.jl threads share a sink; beyond a warp (paired policies only) they
+    // form ws groups of one warp each, group g taking the g-th contiguous
+    // part of every tile: thread = g * (nt / ws) + sink slot * 32 + lane
+    // (several warps per sink exist in the one-sink-per-thread paired kernels)
+    constexpr bool kMultiWarp = is_paired<P>::value && IPT == 1;
+    const int jl = (kMultiWarp && p.jl > 32) ? 32 : p.jl;  // lanes of one warp per sink
+    const int ws = kMultiWarp ? p.jl / jl : 1;            // warps per sink
+    const int nt_g = nt / ws;
+    const int grp = kMultiWarp ? tid / nt_g : 0;
     const int lj = tid & (jl - 1);
-    const int islot = tid / jl;
-    const int slots = nt / jl;
+    const int islot = (tid - grp * nt_g) / jl;
+    const int slots = nt_g / jl;
     const typename P::real eps2 = static_cast<typename P::real>(p.eps2);
-    const int per = p.tile / jl;  // a multiple of P::kChunk (host-checked)
+    const int per = p.tile / p.jl;  // sources per lane and tile, a multiple of P::kChunk (host-checked)
+    const int c0 = kMultiWarp ? grp * (p.tile / ws) : 0;  // this group's part of a tile starts at tile position c0
     constexpr bool kPair = is_paired<P>::value;
     static_assert(kPair || !FUSED, "fused prediction needs a paired policy");
     // the ring holds predicted records (cp.async), or with fused prediction
@@ -1599,6 +1641,8 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     };
 
     __shared__ int s_last;
+    __shared__ float s_gnd[kMaxThreads];  // several warps per sink: the groups' nearest neighbours
+    __shared__ int s_gnid[kMaxThreads];
     for (int round = 0;; ++round) {
         int64_t item;
         if (p.static_items) {
@@ -1701,7 +1745,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 }
                 phase ^= 1u << stage;
                 const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
-                predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);
+                predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);  // (warp lanes)
                 __syncthreads();  // pair records ready, the stage is free again
                 if (tid == 0 && t + nstage < n_tiles) issue(t + nstage, j0, j1);
                 st = pbuf;
@@ -1725,8 +1769,10 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             // a warp whose sink slots are all empty (fewer sinks than the CTA
             // holds) skips the tile and leaves the issue slots to the others
             if (warp_busy) {
-                if (__any_sync(kFull, mine)) tile_loop<P, IPT, true>(st, tb, per, jl, lj, sk, ac, eps2);
-                else tile_loop<P, IPT, false>(st, tb, per, jl, lj, sk, ac, eps2);
+                // the group's part: c0 .. c0 + per * jl, whose (pair) records start c0 records in
+                const unsigned char *sg = st + static_cast<size_t>(c0) * P::RB;
+                if (__any_sync(kFull, mine)) tile_loop<P, IPT, true>(sg, tb + c0, per, jl, lj, sk, ac, eps2);
+                else tile_loop<P, IPT, false>(sg, tb + c0, per, jl, lj, sk, ac, eps2);
             }
             since_flush += per;
             if (since_flush >= P::kFlush) {
@@ -1752,9 +1798,40 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                         nid = ac[k].bid;
                     }
                 }
-                if (!warp_busy) continue;  // no sink of this warp: nothing to merge or write
                 ds q[P::NS];
-                merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, q, nd, nid);
+                if (warp_busy) merge_lanes_ds<P>(tot + k * P::NS * nt, nt, jl, q, nd, nid);
+                if (kMultiWarp && ws > 1) {
+                    // groups 1 .. ws-1 leave their merged totals and neighbour in
+                    // their own slots; group 0 adds them in group order
+                    float2 *t2 = reinterpret_cast<float2 *>(tot + k * P::NS * nt);
+                    if (grp > 0 && warp_busy) {
+#pragma unroll
+                        for (int f = 0; f < P::NS; ++f) t2[f * nt] = make_float2(q[f].h, q[f].l);
+                        if (P::kNN) {
+                            s_gnd[tid] = static_cast<float>(nd);
+                            s_gnid[tid] = nid;
+                        }
+                    }
+                    __syncthreads();
+                    if (grp == 0 && warp_busy) {
+                        for (int g2 = 1; g2 < ws; ++g2) {
+                            const int o = g2 * nt_g;
+#pragma unroll
+                            for (int f = 0; f < P::NS; ++f) q[f] = ds_add(q[f], ds{t2[f * nt + o].x, t2[f * nt + o].y});
+                            if (P::kNN) {
+                                const float od = s_gnd[tid + o];
+                                const int oid = s_gnid[tid + o];
+                                const float d = static_cast<float>(nd);
+                                if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(nid))) {
+                                    nd = static_cast<double>(od);
+                                    nid = oid;
+                                }
+                            }
+                        }
+                    }
+                    __syncthreads();  // the slots are free again
+                }
+                if (!warp_busy || grp > 0) continue;  // nothing (more) to write from this warp
                 const int64_t pi = ii[k] - p.tail_sink0;
                 if (val[k]) write_fields_ds<P>(p, ii[k], isplit, slice, pi, pn, q, jl, lj);
                 if (P::kNN && lj == 0 && val[k]) {
@@ -1823,6 +1900,10 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 __threadfence();
                 reduce_iblock<P>(p, iblk);
                 if (tid == 0) p.done[iblk] = 0u;  // ready for the next launch
+                // the i-block's partial sums are consumed: their L2 lines need
+                // no write-back to DRAM
+                __syncthreads();
+                discard_partials<P>(p, iblk);
             }
         }
     }

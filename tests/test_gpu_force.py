@@ -166,7 +166,10 @@ def test_fused_prediction_small_n_active(sp2, oracle_mod, order):
                                   # are fetched while the current one is evaluated (ragged last tiles)
                                   (1, dict(threads=256, i_per_thread=1, j_lanes=32, j_tile=512, split_j=5), True),
                                   (5, dict(threads=128, i_per_thread=1, j_lanes=16, j_tile=256, split_j=3), True),
-                                  (64, dict(threads=256, i_per_thread=1, j_lanes=4, j_tile=256, split_j=11), True)):
+                                  (64, dict(threads=256, i_per_thread=1, j_lanes=4, j_tile=256, split_j=11), True),
+                                  # several warps per sink, each on its own part of every tile
+                                  (1, dict(threads=256, i_per_thread=1, j_lanes=128, j_tile=1024, split_j=3), True),
+                                  (3, dict(threads=256, i_per_thread=1, j_lanes=64, j_tile=512, split_j=4), True)):
             idx = np.sort(np.random.default_rng(n_i).choice(n, n_i, replace=False)).astype(np.int32)
             c.predict(s["t"])
             c.set_launch(n_i, dict(shape, ctas_per_sm=0))
@@ -236,3 +239,32 @@ def test_whole_waves_and_split_tail(sp2, oracle_mod, mixed, n, per_sm):
     g = gpu_run(sp2, s, idx, order=4, precision=sp2.SP2_MIXED if mixed else sp2.SP2_FP64, eps2=eps2, launch=launch)
     r = oracle_ref(oracle_mod, s, idx, order=4, eps2=eps2)
     check(g, r, order=4, mixed=mixed, s=s, i_idx=idx, label=f"n={n} per_sm={per_sm}")
+
+
+@pytest.mark.parametrize("n_i,shape", [
+    (1, dict(threads=256, i_per_thread=1, j_lanes=256, j_tile=1024, split_j=1)),
+    (5, dict(threads=128, i_per_thread=1, j_lanes=64, j_tile=512, split_j=6)),
+    (700, dict(threads=256, i_per_thread=1, j_lanes=64, j_tile=512, split_j=2)),
+    (3001, dict(threads=256, i_per_thread=1, j_lanes=128, j_tile=1024, split_j=1)),
+])
+def test_several_warps_per_sink(sp2, oracle_mod, n_i, shape):
+    """j_lanes above 32 (mixed precision): the warps that share a sink take
+    contiguous parts of every tile and their totals and nearest neighbours are
+    added in warp order; both orders, one and several i-blocks, with and
+    without a source split, match the oracle.  FP64 contexts and several sinks
+    per thread refuse the shape."""
+    n, eps2 = 6001, 1e-8
+    for order in (4, 6):
+        s = state(n, 55 + n_i, order=order, salpeter=(order == 6))
+        idx = np.sort(np.random.default_rng(n_i).choice(n, n_i, replace=False)).astype(np.int32)
+        launch = dict(shape, ctas_per_sm=0)
+        g = gpu_run(sp2, s, idx, order=order, precision=sp2.SP2_MIXED, eps2=eps2, launch=launch)
+        r = oracle_ref(oracle_mod, s, idx, order=order, eps2=eps2)
+        check(g, r, order=order, mixed=True, s=s, i_idx=idx, label=f"{order}/{n_i}/{shape}")
+    s = state(n, 56, order=4)
+    with pytest.raises(sp2.SP2Error):
+        gpu_run(sp2, s, np.arange(5, dtype=np.int32), order=4, precision=sp2.SP2_FP64, eps2=eps2,
+                launch=dict(threads=128, i_per_thread=1, j_lanes=64, j_tile=512, split_j=2, ctas_per_sm=0))
+    with pytest.raises(sp2.SP2Error):
+        gpu_run(sp2, s, np.arange(5, dtype=np.int32), order=4, precision=sp2.SP2_MIXED, eps2=eps2,
+                launch=dict(threads=128, i_per_thread=2, j_lanes=64, j_tile=512, split_j=2, ctas_per_sm=0))
