@@ -132,8 +132,8 @@ struct BatchParams {
 enum Kind { K_FORCE = 0, K_VJP = 1 };
 
 // Dynamic shared memory a pass launch may use (the 227 KiB per block of the
-// GPU, less room for the kernels' static shared variables).
-constexpr int kMaxPassSmem = 226 * 1024;
+// GPU, less room for the kernels' static shared variables, about 2.5 KiB).
+constexpr int kMaxPassSmem = 222 * 1024;
 
 // From this many slices on, the split-j reduction runs one warp per sink on
 // the sink-major partial layout (ForceParams::sink_major).
