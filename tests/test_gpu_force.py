@@ -245,7 +245,7 @@ def test_whole_waves_and_split_tail(sp2, oracle_mod, mixed, n, per_sm):
     (1, dict(threads=128, i_per_thread=1, j_lanes=128, j_tile=1024, split_j=1)),
     (5, dict(threads=128, i_per_thread=1, j_lanes=64, j_tile=512, split_j=6)),
     (700, dict(threads=256, i_per_thread=1, j_lanes=64, j_tile=512, split_j=2)),
-    (3001, dict(threads=256, i_per_thread=1, j_lanes=128, j_tile=1024, split_j=1)),
+    (3001, dict(threads=256, i_per_thread=1, j_lanes=64, j_tile=512, split_j=1)),
 ])
 def test_several_warps_per_sink(sp2, oracle_mod, n_i, shape):
     """j_lanes above 32 (mixed precision): the warps that share a sink take
