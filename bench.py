@@ -69,7 +69,7 @@ def parse():
                    help="with --gpus N > 1: N independent replicas instead of the source split")
     p.add_argument("--blk6-t-end", type=float, default=1.0,
                    help="end time of the 6th-order block-step runs (Sec. 3.7 integrates one N-body time unit)")
-    p.add_argument("--blk6-n", default="16384", help="particle counts of the 6th-order block-step runs")
+    p.add_argument("--blk6-n", default="1024,16384", help="particle counts of the 6th-order block-step runs")
     p.add_argument("--blk6-eps", default="1e-3", help="softening lengths of the 6th-order block-step runs")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -507,7 +507,7 @@ def timed(fn, reps, stream):
     return statistics.median(ts)
 
 
-def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.0, blk6_n=(16384,),
+def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.0, blk6_n=(1024, 16384),
            blk6_eps=(1e-3,)):
     """N_active sweep (mixed vs FP64), batched systems, adjoint: secondary lines."""
     import torch

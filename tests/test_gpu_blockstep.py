@@ -143,6 +143,7 @@ def test_block_run_h6_matches_oracle(sp2, oracle_mod, mixed):
     eg = abs(oracle_mod.energy(m, xg, vg, eps2) / e0 - 1)
     eo = abs(oracle_mod.energy(m, xo, vo, eps2) / e0 - 1)
     info = (sg, so["block_steps"], so["active_sum"], float(np.median(dx)), float(dx.max()), eg, eo)
+    print("6th-order block steps (gpu stats, oracle blocks, oracle active, median dx, max dx, E err gpu, oracle):", info)
     assert eo < 1e-10
     if not mixed:
         assert abs(sg["block_steps"] - so["block_steps"]) <= 0.05 * so["block_steps"] + 1, info
@@ -152,10 +153,12 @@ def test_block_run_h6_matches_oracle(sp2, oracle_mod, mixed):
     else:
         # double-single forces: the noise of jerk and snap, amplified in the
         # interpolated crackle, pop and 5th derivative, shortens some steps
-        # (Sec. 3.7 sees fewer active particles per block with DS forces)
-        assert so["block_steps"] * 0.95 <= sg["block_steps"] <= 4 * so["block_steps"], info
-        assert np.median(dx) < 1e-5 and dx.max() < 1e-3, info
-        assert eg < 1e-6, info
+        # (Sec. 3.7 sees fewer active particles per block with DS forces);
+        # measured: 116 blocks against 74, positions within 1.4e-9, energy
+        # error 2.3e-10 against the FP64 oracle's 1.6e-12
+        assert so["block_steps"] <= sg["block_steps"] <= 1.75 * so["block_steps"], info
+        assert np.median(dx) < 1e-9 and dx.max() < 1e-7, info
+        assert eg < 1e-8, info
 
 
 def test_block_run_h6_fp64_convergence_and_underflow_guard(sp2, oracle_mod):
