@@ -379,11 +379,11 @@ struct MixedForce {
     }
     __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(c.th[f]) + static_cast<double>(c.tl[f]);
-        t[NS - 1] = -t[NS - 1];
+        for (int f = 0; f < NS; ++f) t[f] = f2d_exact(c.th[f]) + f2d_exact(c.tl[f]);
+        t[NS - 1] = f2d_exact(-c.th[NS - 1]) + f2d_exact(-c.tl[NS - 1]);
     }
     __device__ static __forceinline__ void nn_acc(const Acc &c, double &d, int &id) {
-        d = (NN && c.bid >= 0) ? static_cast<double>(c.bd) : d_inf();
+        d = (NN && c.bid >= 0) ? f2d_exact(c.bd) : d_inf();
         id = NN ? c.bid : -1;
     }
     template <class Out>
@@ -605,7 +605,7 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
     __device__ static __forceinline__ void totals(const Acc &, const double *tot, int stride, double *t) {
         const float2 *t2 = reinterpret_cast<const float2 *>(tot);
 #pragma unroll
-        for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(t2[f * stride].x) + static_cast<double>(t2[f * stride].y);
+        for (int f = 0; f < NS; ++f) t[f] = f2d_exact(t2[f * stride].x) + f2d_exact(t2[f * stride].y);
         t[NS - 1] = -t[NS - 1];
     }
     // the potential field is summed as +m/r and leaves with its sign changed
@@ -655,11 +655,11 @@ struct MixedPairBatch : MixedPairForce<ORDER, NN> {
     }
     __device__ static __forceinline__ void totals(const Acc &c, const double *, int, double *t) {
 #pragma unroll
-        for (int f = 0; f < NS; ++f) t[f] = static_cast<double>(c.th[f]) + static_cast<double>(c.tl[f]);
-        t[NS - 1] = -t[NS - 1];
+        for (int f = 0; f < NS; ++f) t[f] = f2d_exact(c.th[f]) + f2d_exact(c.tl[f]);
+        t[NS - 1] = f2d_exact(-c.th[NS - 1]) + f2d_exact(-c.tl[NS - 1]);
     }
     __device__ static __forceinline__ void nn_acc(const Acc &c, double &d, int &id) {
-        d = (NN && c.bid >= 0) ? static_cast<double>(c.bd) : d_inf();
+        d = (NN && c.bid >= 0) ? f2d_exact(c.bd) : d_inf();
         id = NN ? c.bid : -1;
     }
 };
@@ -1361,7 +1361,7 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
             }
         }
     }
-    nd = static_cast<double>(d);
+    nd = f2d_exact(d);
 }
 
 // A sink's merged double-single totals leave as FP64 with the fields spread
@@ -1387,8 +1387,11 @@ __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i,
                 l = q[g].l;
             }
         if (f < P::NS) {
-            double v = static_cast<double>(h) + static_cast<double>(l);
-            if (P::kNegLast && f == P::NS - 1) v = -v;
+            if (P::kNegLast && f == P::NS - 1) {
+                h = -h;
+                l = -l;
+            }
+            const double v = f2d_exact(h) + f2d_exact(l);
             if (split == 1) P::store_final(p, i, f, v);
             else if (p.sink_major) p.part[(pi * NF + f) * split + slice] = v;
             else p.part[static_cast<int64_t>(f) * split * pn + static_cast<int64_t>(slice) * pn + pi] = v;
@@ -1794,7 +1797,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
             if constexpr (kPair) {
                 if constexpr (P::kNN) {
                     if (ac[k].bid >= 0) {
-                        nd = static_cast<double>(ac[k].bd);
+                        nd = f2d_exact(ac[k].bd);
                         nid = ac[k].bid;
                     }
                 }
@@ -1823,7 +1826,7 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                                 const int oid = s_gnid[tid + o];
                                 const float d = static_cast<float>(nd);
                                 if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(nid))) {
-                                    nd = static_cast<double>(od);
+                                    nd = f2d_exact(od);
                                     nid = oid;
                                 }
                             }

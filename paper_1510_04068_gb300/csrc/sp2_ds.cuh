@@ -43,6 +43,30 @@ __device__ __forceinline__ ds ds_split(double x) {
 }
 
 
+// The FP64 value of an FP32 number, formed from its bits with integer
+// operations (every FP32 value is exactly a double, so this equals the
+// conversion instruction, subnormals and infinities included) -- GB300 runs
+// FP64 and its conversions at 1/64 of the FP32 rate, and the kernels'
+// epilogues convert many double-single totals.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) {  // inf / nan
+        bits = sign | 0x7ff0000000000000ull | (static_cast<unsigned long long>(m) << 29);
+    } else if (e != 0u) {  // normal: rebias the exponent (127 -> 1023)
+        bits = sign | (static_cast<unsigned long long>(e + 896u) << 52) | (static_cast<unsigned long long>(m) << 29);
+    } else if (m == 0u) {  // signed zero
+        bits = sign;
+    } else {  // subnormal m 2^-149 with its leading one at bit p
+        const unsigned p = 31u - static_cast<unsigned>(__clz(m));
+        bits = sign | (static_cast<unsigned long long>(p + 874u) << 52) |
+               ((static_cast<unsigned long long>(m) << (52u - p)) & 0xfffffffffffffull);
+    }
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // Words of particle j's double-single cache entry (layout in sp2_internal.h)
 // that the predictor uses, loaded into w[0 .. dscache_words) (order 2: words
 // 0, 1 and 3 only).
