@@ -324,15 +324,16 @@ sp2_status run_pass(sp2_ctx *c, int kind, int order, int mixed, int nn, const un
                          static_cast<size_t>(kMaxPassSmem);
     const int fused_stages = (fused && (slice_len <= tile || !two_fit)) ? 1 : kFusedStagesDevice;
     key.fused_stages = fused ? fused_stages : 0;
+    key.mw = jl > 32 ? 1 : 0;
     const size_t smem_total = pass_smem_bytes(kind, order, mixed, tile, rb, L.threads, L.i_per_thread, fused,
                                               fused_stages);
     if (smem_total > static_cast<size_t>(kMaxPassSmem))
         return fail(c, SP2_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory (max %d)", smem_total,
                     kMaxPassSmem);
     if ((tile / jl) % 8 != 0) return fail(c, SP2_ERR_ARG, "j_tile / j_lanes must be a multiple of 8");
-    if (jl > 32 && (!mixed || L.i_per_thread != 1))
+    if (jl > 32 && (!mixed || L.i_per_thread != 1 || kind != K_FORCE))
         return fail(c, SP2_ERR_UNSUPPORTED,
-                    "j_lanes above 32 (several warps per sink) need a mixed-precision context and i_per_thread 1");
+                    "j_lanes above 32 (several warps per sink) need a mixed-precision force pass and i_per_thread 1");
     int per_sm = L.ctas_per_sm;
     if (per_sm <= 0) {
         SP2_CK(c, force_kernel_occupancy(key, L.threads, tile, &per_sm));
@@ -1447,6 +1448,7 @@ sp2_status sp2_autotune(sp2_ctx *c, int64_t n_i, sp2_launch *best) {
         // the kernel run_pass will launch: fused prediction when the sinks fit one i-block
         const int fused = (mixed && c->js.dsc && n_i <= int64_t(L.threads / L.j_lanes) * L.i_per_thread) ? 1 : 0;
         KernelKey key{K_FORCE, order, mixed, nn, L.i_per_thread, fused};
+        key.mw = L.j_lanes > 32 ? 1 : 0;
         // a fused pass that cannot hold two bulk-copy stages runs with one
         if (fused && pass_smem_bytes(K_FORCE, order, mixed, L.j_tile, c->rb, L.threads, L.i_per_thread, 1, 2) >
                          static_cast<size_t>(kMaxPassSmem))

@@ -145,6 +145,12 @@ struct has_fold_tile { static constexpr bool value = false; };
 template <class P>
 struct has_fold_tile<P, decltype(void(&P::fold_tile))> { static constexpr bool value = true; };
 
+// Force policies whose sinks several warps may share define kSharedSinks = true.
+template <class P, class = void>
+struct shares_sinks { static constexpr bool value = false; };
+template <class P>
+struct shares_sinks<P, decltype(void(P::kSharedSinks))> { static constexpr bool value = P::kSharedSinks; };
+
 // Policies that evaluate two sources per step define kPaired = true.
 template <class P, class = void>
 struct is_paired { static constexpr bool value = false; };
@@ -418,6 +424,7 @@ struct MixedPairForce : MixedForce<ORDER, NN> {
     using Base::kKeyMask;
     using typename Base::Rec;
     static constexpr bool kPaired = true;
+    static constexpr bool kSharedSinks = true;
     static constexpr int PRB = 2 * Base::RB;  // bytes of one pair record
     struct PRec {
         float4 w0, w1, w2, w4, w6;  // {xh,yh}, {zh,m}, {xl,yl}, {vx,vy}, [{ax,ay}]
@@ -1585,7 +1592,7 @@ __device__ __forceinline__ void discard_partials(const ForceParams &p, int64_t i
 // records, then (mixed policies) the running totals (8 bytes each: FP64, or a
 // double-single pair in the paired policy), [sink k][field f][thread]
 // so each thread owns its slots.
-template <class P, int IPT, bool FUSED>
+template <class P, int IPT, bool FUSED, bool MW = false>
 __device__ __forceinline__ void pass_body(const ForceParams &p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_item;
@@ -1594,8 +1601,9 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
     // p.jl threads share a sink; beyond a warp (paired policies only) they
     // form ws groups of one warp each, group g taking the g-th contiguous
     // part of every tile: thread = g * (nt / ws) + sink slot * 32 + lane
-    // (several warps per sink exist in the one-sink-per-thread paired kernels)
-    constexpr bool kMultiWarp = is_paired<P>::value && IPT == 1;
+    // (several warps per sink: a kernel of its own, for the one-sink-per-thread
+    // kernels of the paired force policies, so the others keep their registers)
+    constexpr bool kMultiWarp = MW && shares_sinks<P>::value && IPT == 1;
     const int jl = (kMultiWarp && p.jl > 32) ? 32 : p.jl;  // lanes of one warp per sink
     const int ws = kMultiWarp ? p.jl / jl : 1;            // warps per sink
     const int nt_g = nt / ws;
@@ -1960,9 +1968,13 @@ __device__ __forceinline__ void device_shape(ForceParams &q) {
     q.sink_major = q.split >= kWarpReduceMinSplit ? 1 : 0;
 }
 
-template <class P, int IPT, bool FUSED, bool DEVN = false>
+// MODE 0: the pass; 1: the device-count form; 2: several warps per sink.
+template <class P, int IPT, bool FUSED, int MODE = 0>
 __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
-    if constexpr (DEVN) {
+    constexpr bool DEVN = MODE == 1;
+    if constexpr (MODE == 2) {
+        pass_body<P, IPT, FUSED, true>(p);
+    } else if constexpr (DEVN) {
         static_assert(IPT == 1 && !FUSED, "the device-count form takes one sink per thread");
         ForceParams q = p;
         device_shape(q);
@@ -2169,7 +2181,7 @@ inline size_t pass_smem(size_t tile, int threads, int fused_stages = kFusedStage
 
 constexpr int kMaxDynSmem = kMaxPassSmem;
 
-template <class P, int IPT, bool FUSED, bool DEVN = false>
+template <class P, int IPT, bool FUSED, int DEVN = 0>
 inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size_t tile, cudaStream_t s) {
     static bool attr_set = false;
     const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads, p.fused_stages);
@@ -2184,7 +2196,7 @@ inline cudaError_t launch_pass(const ForceParams &p, int grid, int threads, size
     return cudaGetLastError();
 }
 
-template <class P, int IPT, bool FUSED, bool DEVN = false>
+template <class P, int IPT, bool FUSED, int DEVN = 0>
 inline cudaError_t occupancy_pass(int threads, size_t tile, int *blocks, int fused_stages = 0) {
     const size_t smem = pass_smem<P, IPT, FUSED>(tile, threads, fused_stages > 0 ? fused_stages : kFusedStages);
     if (smem > static_cast<size_t>(kMaxDynSmem)) {
@@ -2212,7 +2224,16 @@ struct takes_device_count<Fp64Force<6, false>> { static constexpr bool value = t
 
 template <class P, bool FUSED>
 inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                                  cudaStream_t s, int *blocks, int fstages = 0) {
+                                  cudaStream_t s, int *blocks, int fstages = 0, int mw = 0) {
+    if (mw) {  // several warps per sink: one sink per thread, paired force policies
+        if constexpr (shares_sinks<P>::value) {
+            if (ipt != 1) return cudaErrorInvalidValue;
+            return occ ? occupancy_pass<P, 1, FUSED, 2>(threads, tile, blocks, fstages)
+                       : launch_pass<P, 1, FUSED, 2>(*p, grid, threads, tile, s);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     switch (ipt) {
         case 1: return occ ? occupancy_pass<P, 1, FUSED>(threads, tile, blocks, fstages) : launch_pass<P, 1, FUSED>(*p, grid, threads, tile, s);
         case 2: return occ ? occupancy_pass<P, 2, FUSED>(threads, tile, blocks, fstages) : launch_pass<P, 2, FUSED>(*p, grid, threads, tile, s);
@@ -2224,33 +2245,46 @@ inline cudaError_t dispatch_ipt_f(bool occ, int ipt, const ForceParams *p, int g
 // fused = 1 is available for the mixed force policies only
 template <class P>
 inline cudaError_t dispatch_ipt(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                                cudaStream_t s, int *blocks, int fused = 0, int devn = 0, int fstages = 0) {
+                                cudaStream_t s, int *blocks, int fused = 0, int devn = 0, int fstages = 0,
+                                int mw = 0) {
     if constexpr (takes_device_count<P>::value) {
         if (devn) {
-            if (ipt != 1 || fused) return cudaErrorInvalidValue;
-            return occ ? occupancy_pass<P, 1, false, true>(threads, tile, blocks)
-                       : launch_pass<P, 1, false, true>(*p, grid, threads, tile, s);
+            if (ipt != 1 || fused || mw) return cudaErrorInvalidValue;
+            return occ ? occupancy_pass<P, 1, false, 1>(threads, tile, blocks)
+                       : launch_pass<P, 1, false, 1>(*p, grid, threads, tile, s);
         }
     } else {
         if (devn) return cudaErrorInvalidValue;
     }
     if constexpr (P::kCanFuse && is_paired<P>::value) {
-        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, tile, s, blocks, fstages);
+        if (fused) return dispatch_ipt_f<P, true>(occ, ipt, p, grid, threads, tile, s, blocks, fstages, mw);
     } else {
         if (fused) return cudaErrorInvalidValue;
     }
-    return dispatch_ipt_f<P, false>(occ, ipt, p, grid, threads, tile, s, blocks);
+    return dispatch_ipt_f<P, false>(occ, ipt, p, grid, threads, tile, s, blocks, 0, mw);
 }
 
 // Neighbour-list kernels exist for one sink per thread only.
 template <class P>
 inline cudaError_t dispatch_nb(bool occ, int ipt, const ForceParams *p, int grid, int threads, size_t tile,
-                               cudaStream_t s, int *blocks, int fused, int fstages = 0) {
+                               cudaStream_t s, int *blocks, int fused, int fstages = 0, int mw = 0) {
     if (ipt != 1) return cudaErrorInvalidValue;
     if constexpr (P::kCanFuse && is_paired<P>::value) {
-        if (fused) return occ ? occupancy_pass<P, 1, true>(threads, tile, blocks, fstages) : launch_pass<P, 1, true>(*p, grid, threads, tile, s);
+        if (fused && mw)
+            return occ ? occupancy_pass<P, 1, true, 2>(threads, tile, blocks, fstages)
+                       : launch_pass<P, 1, true, 2>(*p, grid, threads, tile, s);
+        if (fused)
+            return occ ? occupancy_pass<P, 1, true>(threads, tile, blocks, fstages)
+                       : launch_pass<P, 1, true>(*p, grid, threads, tile, s);
     } else {
         if (fused) return cudaErrorInvalidValue;
+    }
+    if (mw) {
+        if constexpr (shares_sinks<P>::value)
+            return occ ? occupancy_pass<P, 1, false, 2>(threads, tile, blocks)
+                       : launch_pass<P, 1, false, 2>(*p, grid, threads, tile, s);
+        else
+            return cudaErrorInvalidValue;
     }
     return occ ? occupancy_pass<P, 1, false>(threads, tile, blocks) : launch_pass<P, 1, false>(*p, grid, threads, tile, s);
 }
@@ -2296,23 +2330,24 @@ inline cudaError_t occupancy_batched(int threads, int *blocks) {
                                       size_t tile, cudaStream_t s) {                                       \
         if (k.nb)                                                                                          \
             return k.nn ? dispatch_nb<WithNeighbours<POLICY<ORDER, true>>>(false, k.ipt, &p, grid, threads,  \
-                                                                           tile, s, nullptr, k.fused)      \
+                                                                           tile, s, nullptr, k.fused, 0,   \
+                                                                           k.mw)                           \
                         : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(false, k.ipt, &p, grid, threads, tile, s, nullptr,  \
-                                                        k.fused, k.devn)                                   \
+                                                        k.fused, k.devn, 0, k.mw)                          \
                     : dispatch_ipt<POLICY<ORDER, false>>(false, k.ipt, &p, grid, threads, tile, s, nullptr, \
-                                                         k.fused, k.devn);                                 \
+                                                         k.fused, k.devn, 0, k.mw);                        \
     }                                                                                                      \
     cudaError_t occupancy_force_##SUFFIX(const KernelKey &k, int threads, size_t tile, int *blocks) {       \
         if (k.nb)                                                                                          \
             return k.nn ? dispatch_nb<WithNeighbours<POLICY<ORDER, true>>>(true, k.ipt, nullptr, 0, threads, \
                                                                            tile, 0, blocks, k.fused,        \
-                                                                           k.fused_stages)                  \
+                                                                           k.fused_stages, k.mw)            \
                         : cudaErrorInvalidValue;                                                           \
         return k.nn ? dispatch_ipt<POLICY<ORDER, true>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks,  \
-                                                        k.fused, k.devn, k.fused_stages)                   \
+                                                        k.fused, k.devn, k.fused_stages, k.mw)             \
                     : dispatch_ipt<POLICY<ORDER, false>>(true, k.ipt, nullptr, 0, threads, tile, 0, blocks, \
-                                                         k.fused, k.devn, k.fused_stages);                 \
+                                                         k.fused, k.devn, k.fused_stages, k.mw);           \
     }                                                                                                      \
     cudaError_t launch_reduce_##SUFFIX(const KernelKey &k, const ReduceParams &r, cudaStream_t s) {        \
         return k.nn ? launch_reduce<POLICY<ORDER, true>>(r, s) : launch_reduce<POLICY<ORDER, false>>(r, s); \

@@ -151,6 +151,7 @@ struct KernelKey {
     int nb;     // 1: neighbour lists (force kernels with nearest neighbour, ipt 1)
     int devn;   // 1: sink count read on the device, shape derived from it (order 4 or 6, no NN, ipt 1)
     int fused_stages;  // fused: bulk-copy stages the launch uses (0: the maximum), for the occupancy query
+    int mw;     // 1: several warps per sink (j_lanes above 32; one sink per thread, paired force policies)
 };
 
 // Each kernel translation unit provides these for its (order, precision).
