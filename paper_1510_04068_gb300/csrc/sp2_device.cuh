@@ -6,9 +6,11 @@
 // Method (Sec. 2.1 of the paper): one thread (or j_lanes threads, the paper's
 // 2D thread blocks) per sink, the sources of a slice streamed through shared
 // memory; when the sinks are few the sources are split into slices (the
-// source-split method) so that every SM has work, and a second kernel combines
-// the slices (Sec. 2.2.4 describes both that two-kernel form and an atomic
-// form; this library uses the deterministic two-kernel form).
+// source-split method) so that every SM has work, and the slices are combined
+// in a fixed order, either by the last CTA of each block of sinks to finish
+// (found with an atomic counter) or by a second kernel (Sec. 2.2.4 describes
+// a two-kernel form and an atomic form); either way the result does not
+// depend on scheduling.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +33,10 @@ __device__ __forceinline__ double d_inf() { return __longlong_as_double(0x7ff000
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// bring the L1 line holding p in ahead of its load
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -138,6 +144,89 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return d;
 }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// Double-single steps on f32x2 pairs: two particles' values side by side,
+// each half rounded exactly as the scalar steps of sp2_ds.cuh round it.
+// The error-free steps need every product that feeds a sum rounded on its
+// own; the code generator has been seen to fuse a packed multiply into a
+// following packed add despite the explicit rounding mode (measured: the
+// last bits of the low words then differ from the scalar predictor's), so
+// such products are formed with scalar multiplies, which it leaves alone.
+__device__ __forceinline__ float2 mul2_sep(float2 a, float2 b) {
+    return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+struct ds2 {
+    float2 h, l;
+};
+__device__ __forceinline__ ds2 two_sum2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ ds2 fast_two_sum2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ ds2 ds_add2(ds2 a, ds2 b) {
+    const ds2 s = two_sum2(a.h, b.h);
+    return fast_two_sum2(s.h, add2(s.l, add2(a.l, b.l)));
+}
+__device__ __forceinline__ ds2 ds_add_f2(ds2 a, float2 b) {
+    const ds2 s = two_sum2(a.h, b);
+    return fast_two_sum2(s.h, add2(s.l, a.l));
+}
+__device__ __forceinline__ ds2 ds_mul2(ds2 a, ds2 b) {
+    const float2 p = mul2_sep(a.h, b.h);
+    float2 e = fma2(a.h, b.h, make_float2(-p.x, -p.y));
+    e = fma2(a.h, b.l, fma2(a.l, b.h, e));
+    return fast_two_sum2(p, e);
+}
+
+// predict_ds_words (sp2_ds.cuh) for two particles at once, a in the .x halves
+// and b in the .y halves: the same operations in the same order, so each
+// record equals the scalar predictor's bit for bit.
+template <int ORDER>
+__device__ __forceinline__ void predict_ds_words2(const float4 *wa, const float4 *wb, float t_hi, float t_lo,
+                                                  float4 *oa, float4 *ob) {
+    if (ORDER == 2) {
+        predict_ds_words<ORDER>(wa, t_hi, t_lo, oa);
+        predict_ds_words<ORDER>(wb, t_hi, t_lo, ob);
+        return;
+    }
+    auto pk = [](const float4 &x, const float4 &y, int c) {
+        return c == 0 ? make_float2(x.x, y.x) : (c == 1 ? make_float2(x.y, y.y) : make_float2(x.z, y.z));
+    };
+    const ds2 dt = ds_add2(ds2{dup2(t_hi), dup2(t_lo)}, ds2{make_float2(-wa[1].w, -wb[1].w), make_float2(-wa[2].w, -wb[2].w)});
+    const float2 half = dup2(0.5f), sixth = dup2(1.f / 6.f), c24 = dup2(1.f / 24.f);
+    float2 oh[3], ol[3], ov[3], oc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 xh = pk(wa[0], wb[0], c), xl = pk(wa[1], wb[1], c);
+        const float2 vh = pk(wa[2], wb[2], c), vl = pk(wa[3], wb[3], c);
+        const float2 ah = pk(wa[4], wb[4], c), al = pk(wa[5], wb[5], c);
+        const float2 jk = pk(wa[6], wb[6], c);
+        float2 sn = dup2(0.f);
+        if constexpr (ORDER == 6) sn = pk(wa[7], wb[7], c);
+        const float2 jx = (ORDER == 6) ? fma2(mul2(dt.h, c24), sn, mul2(jk, sixth)) : mul2(jk, sixth);
+        // (the halvings are exact, so a fused form of them rounds alike)
+        const ds2 cx = ds_add_f2(ds2{mul2(half, ah), mul2(half, al)}, mul2_sep(dt.h, jx));
+        const ds2 bx = ds_add2(ds2{vh, vl}, ds_mul2(dt, cx));
+        const ds2 px = ds_add2(ds2{xh, xl}, ds_mul2(dt, bx));
+        oh[c] = px.h;
+        ol[c] = px.l;
+        const float2 jv = (ORDER == 6) ? fma2(mul2(dt.h, sixth), sn, mul2(half, jk)) : mul2(half, jk);
+        ov[c] = add2(vh, fma2(dt.h, fma2(dt.h, jv, add2(ah, al)), vl));
+        oc[c] = (ORDER == 6) ? add2(ah, fma2(dt.h, fma2(dt.h, mul2(half, sn), jk), al)) : dup2(0.f);
+    }
+    oa[0] = make_float4(oh[0].x, oh[1].x, oh[2].x, wa[0].w);
+    ob[0] = make_float4(oh[0].y, oh[1].y, oh[2].y, wb[0].w);
+    oa[1] = make_float4(ol[0].x, ol[1].x, ol[2].x, wa[3].w);
+    ob[1] = make_float4(ol[0].y, ol[1].y, ol[2].y, wb[3].w);
+    oa[2] = make_float4(ov[0].x, ov[1].x, ov[2].x, 0.f);
+    ob[2] = make_float4(ov[0].y, ov[1].y, ov[2].y, 0.f);
+    oa[3] = make_float4(oc[0].x, oc[1].x, oc[2].x, 0.f);
+    ob[3] = make_float4(oc[0].y, oc[1].y, oc[2].y, 0.f);
+}
 
 // Policies whose chunk fold reads the chunk's records (batched kernel).
 template <class P, class = void>
@@ -257,6 +346,17 @@ struct MixedForce {
 #pragma unroll
         for (int k = 0; k < NW; ++k) r.w[k] = o[k];
         return r;
+    }
+    // two sources' records from their words, in packed f32x2 steps
+    __device__ static __forceinline__ void predict_raw2(const float4 *wa, const float4 *wb, float t_hi, float t_lo,
+                                                        Rec &ra, Rec &rb) {
+        float4 oa[4], ob[4];
+        predict_ds_words2<ORDER>(wa, wb, t_hi, t_lo, oa, ob);
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            ra.w[k] = oa[k];
+            rb.w[k] = ob[k];
+        }
     }
     __device__ static __forceinline__ void sink_from(const Rec &r, Sink &s) {
         s.xh = r.w[0].x; s.yh = r.w[0].y; s.zh = r.w[0].z;
@@ -1230,22 +1330,6 @@ __device__ __forceinline__ void load_tile(const ForceParams &p, unsigned char *s
     }
 }
 
-// Source c of a tile as half (m & 1) of pair record (m >> 1) * jl + lj of q,
-// with lj = c & (jl - 1) and m = c / jl (the layout tile_loop reads).
-template <class P>
-__device__ __forceinline__ void put_pair_half(unsigned char *q, int c, int jl, const typename P::Rec &r) {
-    constexpr int W = P::RB / 16;
-    const int lj = c & (jl - 1), m = c / jl;
-    float *d = reinterpret_cast<float *>(q + static_cast<size_t>((m >> 1) * jl + lj) * P::PRB) + (m & 1);
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        d[8 * w] = r.w[w].x;
-        d[8 * w + 2] = r.w[w].y;
-        d[8 * w + 4] = r.w[w].z;
-        d[8 * w + 6] = r.w[w].w;
-    }
-}
-
 template <class P>
 __device__ __forceinline__ typename P::Rec filler_rec() {
     constexpr int W = P::RB / 16;
@@ -1260,24 +1344,34 @@ __device__ __forceinline__ typename P::Rec filler_rec() {
 
 // Fused prediction of a tile whose double-single cache words (kRawWords
 // float4s per source, sources 0 .. cnt-1) a bulk copy has put in shared
-// memory at raw: every thread predicts sources tid, tid + blockDim.x, ... and
-// writes them as pair records; the rest of the tile becomes filler records.
+// memory at raw: thread t predicts the two sources of pair records t,
+// t + blockDim.x, ... together (packed f32x2 steps) and writes each pair
+// record whole; positions past cnt become filler records.
 template <class P>
 __device__ __forceinline__ void predict_staged_tile(const ForceParams &p, const float4 *raw, int cnt,
                                                     unsigned char *q, int jl) {
     constexpr int RW = P::kRawWords;
-#pragma unroll 2
-    for (int c = threadIdx.x; c < p.tile; c += blockDim.x) {
-        typename P::Rec r;
-        if (c < cnt) {
-            float4 w[RW];
+    constexpr int W = P::RB / 16;
+    const int npair = p.tile >> 1;
+    const int lg = __ffs(jl) - 1;  // jl is a power of two
+#pragma unroll 1
+    for (int pr = threadIdx.x; pr < npair; pr += blockDim.x) {
+        // pair pr = k * jl + lj holds tile positions a = lj + 2k jl and a + jl
+        const int k = pr >> lg, lj = pr & (jl - 1);
+        const int a = lj + 2 * k * jl, b = a + jl;
+        float4 wa[RW], wb[RW];
 #pragma unroll
-            for (int k = 0; k < RW; ++k) w[k] = raw[c * RW + k];
-            r = P::predict_raw(w, p.t_hi, p.t_lo);
-        } else {
-            r = filler_rec<P>();
+        for (int w = 0; w < RW; ++w) {
+            wa[w] = (a < cnt) ? raw[a * RW + w] : make_float4(0.f, 0.f, 0.f, 0.f);
+            wb[w] = (b < cnt) ? raw[b * RW + w] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        put_pair_half<P>(q, c, jl, r);
+        typename P::Rec ra, rb;
+        P::predict_raw2(wa, wb, p.t_hi, p.t_lo, ra, rb);
+        if (a >= cnt) ra = filler_rec<P>();
+        if (b >= cnt) rb = filler_rec<P>();
+        unsigned char *d = q + static_cast<size_t>(pr) * P::PRB;
+#pragma unroll
+        for (int w = 0; w < W; ++w) P::store_pair_word(ra.w[w], rb.w[w], w, d);
     }
 }
 
@@ -1371,13 +1465,13 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
     nd = f2d_exact(d);
 }
 
-// A sink's merged double-single totals leave as FP64 with the fields spread
-// over its jl lanes (lane lj takes fields lj, lj + jl, ...): each lane picks
-// its field with FP32 selects, so one conversion per round serves up to jl
-// fields -- GB300 runs FP64 at 1/64 of the FP32 rate.  Field f goes to the
-// final outputs (split == 1, P::store_final) or to the slice's partial-sum
-// slot; with P::kNegLast the last field changes sign (the force policies sum
-// the potential as +m/r).
+// A sink's merged double-single totals leave with the fields spread over its
+// jl lanes (lane lj takes fields lj, lj + jl, ...; each lane picks its field
+// with FP32 selects).  Field f goes to the final outputs as FP64 (split == 1,
+// P::store_final) or, as the double-single pair itself, to the slice's
+// partial-sum slot (8 bytes, like an FP64 partial; the reduction adds the
+// pairs in double-single, see SliceSum); with P::kNegLast the last field
+// changes sign (the force policies sum the potential as +m/r).
 // split == 1: final outputs of sink i; else the partial-sum slot of the
 // slice for partial row pi of pn (the sinks that have partials).
 template <class P>
@@ -1398,63 +1492,95 @@ __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i,
                 h = -h;
                 l = -l;
             }
-            const double v = f2d_exact(h) + f2d_exact(l);
-            if (split == 1) P::store_final(p, i, f, v);
-            else if (p.sink_major) p.part[(pi * NF + f) * split + slice] = v;
-            else p.part[static_cast<int64_t>(f) * split * pn + static_cast<int64_t>(slice) * pn + pi] = v;
+            if (split == 1) {
+                P::store_final(p, i, f, f2d_exact(h) + f2d_exact(l));
+            } else {
+                const int64_t at = p.sink_major ? (pi * NF + f) * split + slice
+                                                : static_cast<int64_t>(f) * split * pn + static_cast<int64_t>(slice) * pn + pi;
+                reinterpret_cast<float2 *>(p.part)[at] = make_float2(h, l);
+            }
         }
     }
 }
 
-// FP64 reduction of one sink's slices (sink-major row: field f's slices are
-// contiguous) by the whole CTA, fields spread over the warps (two at a time): lane l of a
-// warp sums slices l, l+32, ... of a field in order, a fixed xor-butterfly
-// combines the lanes, and the field totals meet in shared memory, where
-// thread 0 writes the outputs (write(t, d, id)).  Different warps work on
-// different fields at the same time, so the 1/64-rate FP64 adds run side by
-// side on the SM's sub-partitions.  The nearest-neighbour field (non-negative r^2, FP64) is
-// merged by comparing bit patterns as integers, which orders them like the
-// values.  Deterministic: the order of every sum is fixed.
+// One field's sum over source slices, added in slice order.  Policies that
+// keep double-single totals (the paired mixed policies) leave their slice
+// partials as double-single pairs and they are added in double-single on the
+// FP32 pipe: GB300 runs FP64 at 1/64 of the FP32 rate, and a split pass with
+// few sinks has one CTA add hundreds of slices per field.  A double-single
+// add keeps ~2^-46 of the larger operand, far below the FP32 terms' own
+// rounding; the total leaves as the exact FP64 value of the pair.  The FP64
+// policies add FP64 partials in FP64.  Either way the order is fixed, so the
+// result does not depend on scheduling.
+template <bool DSP>
+struct SliceSum;
+template <>
+struct SliceSum<false> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add_lane(int off) { v += __shfl_xor_sync(kFull, v, off); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct SliceSum<true> {
+    ds v{0.f, 0.f};
+    // x holds the pair's bits: .h in the low word, .l in the high word
+    __device__ __forceinline__ void add(double x) {
+        v = ds_add(v, ds{__int_as_float(__double2loint(x)), __int_as_float(__double2hiint(x))});
+    }
+    __device__ __forceinline__ void add_lane(int off) {
+        v = ds_add(v, ds{__shfl_xor_sync(kFull, v.h, off), __shfl_xor_sync(kFull, v.l, off)});
+    }
+    __device__ __forceinline__ double value() const { return f2d_exact(v.h) + f2d_exact(v.l); }
+};
+template <class P>
+using slice_sum_t = SliceSum<is_paired<P>::value>;
+
+// Reduction of one sink's slices (sink-major row: field f's slices are
+// contiguous) by the whole CTA, fields spread over the warps (two at a time):
+// lane l of a warp sums slices l, l+32, ... of a field in order (SliceSum), a
+// fixed xor-butterfly combines the lanes, and the field totals meet in shared
+// memory, where thread 0 writes the outputs (write(t, d, id)).  The
+// nearest-neighbour field (non-negative r^2, FP64) is merged by comparing bit
+// patterns as integers, which orders them like the values.  Deterministic:
+// the order of every sum is fixed.
 template <class P, class Write>
 __device__ __forceinline__ void reduce_sink_fields(const double *row, const int32_t *row_id, int split, double *s_f,
                                                    long long &s_nd, int &s_nid, const Write &write) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     // sums: warp w takes fields w, w + nw, ... two at a time with their adds
-    // interleaved (independent FP64 chains keep the FP64 pipe busy)
+    // interleaved (independent chains)
     for (int f0 = warp; f0 < P::NS; f0 += 2 * nw) {
-        bool on[2];
-        const double *col[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            on[q] = f0 + q * nw < P::NS;
-            col[q] = row + static_cast<int64_t>(on[q] ? f0 + q * nw : f0) * split;
-        }
+        const bool two = f0 + nw < P::NS;  // (warp-uniform)
+        const double *col0 = row + static_cast<int64_t>(f0) * split;
+        const double *col1 = row + static_cast<int64_t>(two ? f0 + nw : f0) * split;
         // lane l adds slices l, l + 32, l + 64, ... in that order; the loads of
         // 256 slices per field are all issued before the first add
-        double v[2] = {0.0, 0.0};
+        slice_sum_t<P> v0, v1;
         for (int s0 = 0; s0 < split; s0 += 8 * 32) {
-            double x[2][8];
+            double x0[8], x1[8];
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+            for (int e = 0; e < 8; ++e) {
+                const int s = s0 + lane + 32 * e;
+                x0[e] = (s < split) ? __ldcg(col0 + s) : 0.0;
+                x1[e] = (two && s < split) ? __ldcg(col1 + s) : 0.0;
+            }
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int s = s0 + lane + 32 * e;
-                    x[q][e] = (on[q] && s < split) ? __ldcg(col[q] + s) : 0.0;
+            for (int e = 0; e < 8; ++e)
+                if (s0 + lane + 32 * e < split) {
+                    v0.add(x0[e]);
+                    if (two) v1.add(x1[e]);
                 }
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    if (s0 + lane + 32 * e < split) v[q] += x[q][e];
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (on[q]) s_f[f0 + q * nw] = v[q];
+        for (int off = 16; off > 0; off >>= 1) {
+            v0.add_lane(off);
+            if (two) v1.add_lane(off);
+        }
+        if (lane == 0) {
+            s_f[f0] = v0.value();
+            if (two) s_f[f0 + nw] = v1.value();
+        }
     }
     if (P::kNN && warp == nw - 1) {
         const double *col = row + static_cast<int64_t>(P::NS) * split;
@@ -1513,9 +1639,7 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     if (!p.sink_major) {
         const int64_t stride = static_cast<int64_t>(split) * pn;
         for (int64_t i = b0 + tid; i < b1; i += nt) {
-            double t[P::NS];
-#pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+            slice_sum_t<P> t[P::NS];
             double nd = d_inf();
             int nid = -1;
             const double *base = p.part + (i - r0);       // slice 0, field 0 of this sink's row
@@ -1523,10 +1647,13 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
 #pragma unroll 2
             for (int s = 0; s < split; ++s, base += pn, base_id += pn) {
 #pragma unroll
-                for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(base + f * stride);
+                for (int f = 0; f < P::NS; ++f) t[f].add(__ldcg(base + f * stride));
                 if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(base_id));
             }
-            P::write_final(p, i, t, nd, nid);
+            double v[P::NS];
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
+            P::write_final(p, i, v, nd, nid);
         }
         return;
     }
@@ -1541,27 +1668,28 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     for (int64_t i = b0 + warp; i < b1; i += nw) {
         const double *row = p.part + (i - r0) * NF * split;
         const int32_t *row_id = p.part_id + (i - r0) * split;
-        double t[P::NS];
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+        slice_sum_t<P> t[P::NS];
         double nd = d_inf();
         int nid = -1;
         for (int s = lane; s < split; s += 32) {
 #pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(row + f * split + s);
+            for (int f = 0; f < P::NS; ++f) t[f].add(__ldcg(row + f * split + s));
             if (P::kNN) nn_merge(nd, nid, __ldcg(row + P::NS * split + s), __ldcg(row_id + s));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+            for (int f = 0; f < P::NS; ++f) t[f].add_lane(off);
             if (P::kNN) {
                 const double od = __shfl_xor_sync(kFull, nd, off);
                 const int oid = __shfl_xor_sync(kFull, nid, off);
                 nn_merge(nd, nid, od, oid);
             }
         }
-        if (lane == 0) P::write_final(p, i, t, nd, nid);
+        double v[P::NS];
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
+        if (lane == 0) P::write_final(p, i, v, nd, nid);
     }
 }
 
@@ -1729,8 +1857,16 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                     val[k] = false;
                 }
                 const int slot = val[k] ? raw : static_cast<int>(p.j_begin);
-                if constexpr (FUSED && P::kCanFuse) P::sink_from(P::predict(p.dsc, slot, p.t_hi, p.t_lo), sk[k]);
-                else P::load_sink(p.rec, slot, sk[k]);
+                // fused: the sink's cache words are only prefetched here; it is
+                // predicted after the first tile, so the fetch overlaps that
+                // tile's copy and prediction (and holds no registers)
+                if constexpr (FUSED && P::kCanFuse) {
+                    const float4 *w = p.dsc + static_cast<int64_t>(slot) * kRaw;
+                    prefetch_l1(w);
+                    prefetch_l1(w + kRaw - 1);
+                } else {
+                    P::load_sink(p.rec, slot, sk[k]);
+                }
                 sk[k].slot = val[k] ? slot : -1;
             }
             if constexpr (is_nb<P>::value) P::set_nb(sk[k], p, ii[k], val[k]);
@@ -1756,7 +1892,17 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
                 }
                 phase ^= 1u << stage;
                 const int cnt = (tb + p.tile < j1) ? p.tile : static_cast<int>(j1 - tb);
-                predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);  // (warp lanes)
+                predict_staged_tile<P>(p, reinterpret_cast<const float4 *>(smem + stage * ring_stride), cnt, pbuf, jl);
+                if constexpr (P::kCanFuse) {
+                    if (t == 0 && !p.sink_rec) {
+#pragma unroll
+                        for (int k = 0; k < IPT; ++k) {
+                            const int slot = sk[k].slot;
+                            P::sink_from(P::predict(p.dsc, val[k] ? slot : static_cast<int>(p.j_begin), p.t_hi, p.t_lo), sk[k]);
+                            sk[k].slot = slot;
+                        }
+                    }
+                }
                 __syncthreads();  // pair records ready, the stage is free again
                 if (tid == 0 && t + nstage < n_tiles) issue(t + nstage, j0, j1);
                 st = pbuf;
@@ -1900,15 +2046,20 @@ __device__ __forceinline__ void pass_body(const ForceParams &p) {
         }
         if (isplit > 1 && p.fused_reduce) {
             // every partial of this CTA is written (barrier); thread 0's fence
-            // then makes them visible device-wide before the CTA is counted
+            // then makes them visible device-wide before the CTA is counted.
+            // The last CTA's thread 0 fences again after the count, and the
+            // barrier orders every thread's reads of the other CTAs' partials
+            // after that fence (one thread fences for the CTA, as in a grid
+            // barrier)
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
-                s_last = (atomicAdd(p.done + iblk, 1u) == static_cast<unsigned>(p.split - 1)) ? 1 : 0;
+                const bool last = atomicAdd(p.done + iblk, 1u) == static_cast<unsigned>(p.split - 1);
+                if (last) __threadfence();
+                s_last = last ? 1 : 0;
             }
             __syncthreads();
             if (s_last) {
-                __threadfence();
                 reduce_iblock<P>(p, iblk);
                 if (tid == 0) p.done[iblk] = 0u;  // ready for the next launch
                 // the i-block's partial sums are consumed: their L2 lines need
@@ -1985,24 +2136,25 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
 }
 
 // Second kernel of the source split: sum the slices of each sink in slice
-// order (deterministic, FP64) and take the lexicographic (r2, id) minimum.
+// order (deterministic; SliceSum) and take the lexicographic (r2, id) minimum.
 template <class P>
 __global__ void reduce_kernel(const ReduceParams r) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= r.n_i) return;
     const int64_t stride = static_cast<int64_t>(r.split) * r.n_i;
-    double t[P::NS];
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    slice_sum_t<P> t[P::NS];
     double nd = d_inf();
     int nid = -1;
     for (int s = 0; s < r.split; ++s) {
         const double *base = r.part + static_cast<int64_t>(s) * r.n_i + i;
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += base[f * stride];
+        for (int f = 0; f < P::NS; ++f) t[f].add(base[f * stride]);
         if (P::kNN) nn_merge(nd, nid, base[P::NS * stride], r.part_id[static_cast<int64_t>(s) * r.n_i + i]);
     }
-    P::write_final(r, i, t, nd, nid);
+    double v[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
+    P::write_final(r, i, v, nd, nid);
 }
 
 // The same reduction with one warp per sink, for many slices, on the
@@ -2017,27 +2169,28 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
     constexpr int NF = P::NS + (P::kNN ? 1 : 0);
     const double *row = r.part + i * NF * r.split;
     const int32_t *row_id = r.part_id + i * r.split;
-    double t[P::NS];
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    slice_sum_t<P> t[P::NS];
     double nd = d_inf();
     int nid = -1;
     for (int s = lane; s < r.split; s += 32) {
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
+        for (int f = 0; f < P::NS; ++f) t[f].add(row[f * r.split + s]);
         if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
+        for (int f = 0; f < P::NS; ++f) t[f].add_lane(off);
         if (P::kNN) {
             const double od = __shfl_xor_sync(kFull, nd, off);
             const int oid = __shfl_xor_sync(kFull, nid, off);
             nn_merge(nd, nid, od, oid);
         }
     }
-    if (lane == 0) P::write_final(r, i, t, nd, nid);
+    double v[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
+    if (lane == 0) P::write_final(r, i, v, nd, nid);
 }
 
 // Few sinks, many slices: one 256-thread block per sink on the sink-major
