@@ -107,10 +107,13 @@ class _Trajectory(torch.autograd.Function):
                 x, v, a, j = (t.clone() for t in fctx.ckpts[seg])
                 first = seg * every
                 last = min(first + every, n_steps)
-                states = []
-                for _ in range(first, last):  # recompute the segment's step inputs
-                    states.append((x.clone(), v.clone(), a.clone(), j.clone()))
+                # recompute the segment's step inputs (the state after its
+                # last step is the next segment's checkpoint: not needed here)
+                states = [(x, v, a, j)]
+                for _ in range(first + 1, last):
+                    x, v, a, j = (t.clone() for t in states[-1])
                     sim.ctx.hermite4_step(dt, m, x, v, a, j)
+                    states.append((x, v, a, j))
                 for xs, vs, as_, js in reversed(states):
                     sim.ctx.hermite4_step_vjp(dt, m, xs, vs, as_, js, gx, gv, ga, gj, gm)
             # the initial acc / jerk are forces of (x0, v0, m)

@@ -1465,13 +1465,14 @@ __device__ __forceinline__ void merge_lanes_ds(const double *tot, int stride, in
     nd = f2d_exact(d);
 }
 
-// A sink's merged double-single totals leave with the fields spread over its
-// jl lanes (lane lj takes fields lj, lj + jl, ...; each lane picks its field
-// with FP32 selects).  Field f goes to the final outputs as FP64 (split == 1,
-// P::store_final) or, as the double-single pair itself, to the slice's
-// partial-sum slot (8 bytes, like an FP64 partial; the reduction adds the
-// pairs in double-single, see SliceSum); with P::kNegLast the last field
-// changes sign (the force policies sum the potential as +m/r).
+// A sink's merged double-single totals leave as FP64 (the exact value of the
+// pair) with the fields spread over its jl lanes (lane lj takes fields lj,
+// lj + jl, ...): each lane picks its field with FP32 selects, so one
+// conversion per round serves up to jl fields -- GB300 runs FP64 at 1/64 of
+// the FP32 rate.  Field f goes to the final outputs (split == 1,
+// P::store_final) or to the slice's partial-sum slot, which the split-j
+// reduction adds in FP64; with P::kNegLast the last field changes sign (the
+// force policies sum the potential as +m/r).
 // split == 1: final outputs of sink i; else the partial-sum slot of the
 // slice for partial row pi of pn (the sinks that have partials).
 template <class P>
@@ -1492,54 +1493,19 @@ __device__ __forceinline__ void write_fields_ds(const ForceParams &p, int64_t i,
                 h = -h;
                 l = -l;
             }
-            if (split == 1) {
-                P::store_final(p, i, f, f2d_exact(h) + f2d_exact(l));
-            } else {
-                const int64_t at = p.sink_major ? (pi * NF + f) * split + slice
-                                                : static_cast<int64_t>(f) * split * pn + static_cast<int64_t>(slice) * pn + pi;
-                reinterpret_cast<float2 *>(p.part)[at] = make_float2(h, l);
-            }
+            const double v = f2d_exact(h) + f2d_exact(l);
+            if (split == 1) P::store_final(p, i, f, v);
+            else if (p.sink_major) p.part[(pi * NF + f) * split + slice] = v;
+            else p.part[static_cast<int64_t>(f) * split * pn + static_cast<int64_t>(slice) * pn + pi] = v;
         }
     }
 }
 
-// One field's sum over source slices, added in slice order.  Policies that
-// keep double-single totals (the paired mixed policies) leave their slice
-// partials as double-single pairs and they are added in double-single on the
-// FP32 pipe: GB300 runs FP64 at 1/64 of the FP32 rate, and a split pass with
-// few sinks has one CTA add hundreds of slices per field.  A double-single
-// add keeps ~2^-46 of the larger operand, far below the FP32 terms' own
-// rounding; the total leaves as the exact FP64 value of the pair.  The FP64
-// policies add FP64 partials in FP64.  Either way the order is fixed, so the
-// result does not depend on scheduling.
-template <bool DSP>
-struct SliceSum;
-template <>
-struct SliceSum<false> {
-    double v = 0.0;
-    __device__ __forceinline__ void add(double x) { v += x; }
-    __device__ __forceinline__ void add_lane(int off) { v += __shfl_xor_sync(kFull, v, off); }
-    __device__ __forceinline__ double value() const { return v; }
-};
-template <>
-struct SliceSum<true> {
-    ds v{0.f, 0.f};
-    // x holds the pair's bits: .h in the low word, .l in the high word
-    __device__ __forceinline__ void add(double x) {
-        v = ds_add(v, ds{__int_as_float(__double2loint(x)), __int_as_float(__double2hiint(x))});
-    }
-    __device__ __forceinline__ void add_lane(int off) {
-        v = ds_add(v, ds{__shfl_xor_sync(kFull, v.h, off), __shfl_xor_sync(kFull, v.l, off)});
-    }
-    __device__ __forceinline__ double value() const { return f2d_exact(v.h) + f2d_exact(v.l); }
-};
-template <class P>
-using slice_sum_t = SliceSum<is_paired<P>::value>;
-
-// Reduction of one sink's slices (sink-major row: field f's slices are
-// contiguous) by the whole CTA, fields spread over the warps (two at a time):
-// lane l of a warp sums slices l, l+32, ... of a field in order (SliceSum), a
-// fixed xor-butterfly combines the lanes, and the field totals meet in shared
+// FP64 reduction of one sink's slices (sink-major row: field f's slices are
+// contiguous) by the whole CTA, fields spread over the warps (two at a time,
+// so that different warps' 1/64-rate FP64 adds run side by side): lane l of
+// a warp sums slices l, l+32, ... of a field in order, a fixed xor-butterfly
+// combines the lanes, and the field totals meet in shared
 // memory, where thread 0 writes the outputs (write(t, d, id)).  The
 // nearest-neighbour field (non-negative r^2, FP64) is merged by comparing bit
 // patterns as integers, which orders them like the values.  Deterministic:
@@ -1556,7 +1522,7 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
         const double *col1 = row + static_cast<int64_t>(two ? f0 + nw : f0) * split;
         // lane l adds slices l, l + 32, l + 64, ... in that order; the loads of
         // 256 slices per field are all issued before the first add
-        slice_sum_t<P> v0, v1;
+        double v0 = 0.0, v1 = 0.0;
         for (int s0 = 0; s0 < split; s0 += 8 * 32) {
             double x0[8], x1[8];
 #pragma unroll
@@ -1568,18 +1534,18 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
 #pragma unroll
             for (int e = 0; e < 8; ++e)
                 if (s0 + lane + 32 * e < split) {
-                    v0.add(x0[e]);
-                    if (two) v1.add(x1[e]);
+                    v0 += x0[e];
+                    if (two) v1 += x1[e];
                 }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            v0.add_lane(off);
-            if (two) v1.add_lane(off);
+            v0 += __shfl_xor_sync(kFull, v0, off);
+            if (two) v1 += __shfl_xor_sync(kFull, v1, off);
         }
         if (lane == 0) {
-            s_f[f0] = v0.value();
-            if (two) s_f[f0 + nw] = v1.value();
+            s_f[f0] = v0;
+            if (two) s_f[f0 + nw] = v1;
         }
     }
     if (P::kNN && warp == nw - 1) {
@@ -1639,7 +1605,9 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     if (!p.sink_major) {
         const int64_t stride = static_cast<int64_t>(split) * pn;
         for (int64_t i = b0 + tid; i < b1; i += nt) {
-            slice_sum_t<P> t[P::NS];
+            double t[P::NS];
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
             double nd = d_inf();
             int nid = -1;
             const double *base = p.part + (i - r0);       // slice 0, field 0 of this sink's row
@@ -1647,13 +1615,10 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
 #pragma unroll 2
             for (int s = 0; s < split; ++s, base += pn, base_id += pn) {
 #pragma unroll
-                for (int f = 0; f < P::NS; ++f) t[f].add(__ldcg(base + f * stride));
+                for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(base + f * stride);
                 if (P::kNN) nn_merge(nd, nid, __ldcg(base + P::NS * stride), __ldcg(base_id));
             }
-            double v[P::NS];
-#pragma unroll
-            for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
-            P::write_final(p, i, v, nd, nid);
+            P::write_final(p, i, t, nd, nid);
         }
         return;
     }
@@ -1668,28 +1633,27 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
     for (int64_t i = b0 + warp; i < b1; i += nw) {
         const double *row = p.part + (i - r0) * NF * split;
         const int32_t *row_id = p.part_id + (i - r0) * split;
-        slice_sum_t<P> t[P::NS];
+        double t[P::NS];
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
         double nd = d_inf();
         int nid = -1;
         for (int s = lane; s < split; s += 32) {
 #pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f].add(__ldcg(row + f * split + s));
+            for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(row + f * split + s);
             if (P::kNN) nn_merge(nd, nid, __ldcg(row + P::NS * split + s), __ldcg(row_id + s));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f].add_lane(off);
+            for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
             if (P::kNN) {
                 const double od = __shfl_xor_sync(kFull, nd, off);
                 const int oid = __shfl_xor_sync(kFull, nid, off);
                 nn_merge(nd, nid, od, oid);
             }
         }
-        double v[P::NS];
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
-        if (lane == 0) P::write_final(p, i, v, nd, nid);
+        if (lane == 0) P::write_final(p, i, t, nd, nid);
     }
 }
 
@@ -2136,25 +2100,24 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) 
 }
 
 // Second kernel of the source split: sum the slices of each sink in slice
-// order (deterministic; SliceSum) and take the lexicographic (r2, id) minimum.
+// order (deterministic, FP64) and take the lexicographic (r2, id) minimum.
 template <class P>
 __global__ void reduce_kernel(const ReduceParams r) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= r.n_i) return;
     const int64_t stride = static_cast<int64_t>(r.split) * r.n_i;
-    slice_sum_t<P> t[P::NS];
+    double t[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
     double nd = d_inf();
     int nid = -1;
     for (int s = 0; s < r.split; ++s) {
         const double *base = r.part + static_cast<int64_t>(s) * r.n_i + i;
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f].add(base[f * stride]);
+        for (int f = 0; f < P::NS; ++f) t[f] += base[f * stride];
         if (P::kNN) nn_merge(nd, nid, base[P::NS * stride], r.part_id[static_cast<int64_t>(s) * r.n_i + i]);
     }
-    double v[P::NS];
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
-    P::write_final(r, i, v, nd, nid);
+    P::write_final(r, i, t, nd, nid);
 }
 
 // The same reduction with one warp per sink, for many slices, on the
@@ -2169,28 +2132,27 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
     constexpr int NF = P::NS + (P::kNN ? 1 : 0);
     const double *row = r.part + i * NF * r.split;
     const int32_t *row_id = r.part_id + i * r.split;
-    slice_sum_t<P> t[P::NS];
+    double t[P::NS];
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
     double nd = d_inf();
     int nid = -1;
     for (int s = lane; s < r.split; s += 32) {
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f].add(row[f * r.split + s]);
+        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
         if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f].add_lane(off);
+        for (int f = 0; f < P::NS; ++f) t[f] += __shfl_xor_sync(kFull, t[f], off);
         if (P::kNN) {
             const double od = __shfl_xor_sync(kFull, nd, off);
             const int oid = __shfl_xor_sync(kFull, nid, off);
             nn_merge(nd, nid, od, oid);
         }
     }
-    double v[P::NS];
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) v[f] = t[f].value();
-    if (lane == 0) P::write_final(r, i, v, nd, nid);
+    if (lane == 0) P::write_final(r, i, t, nd, nid);
 }
 
 // Few sinks, many slices: one 256-thread block per sink on the sink-major
