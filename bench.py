@@ -604,8 +604,12 @@ def sweep(sp2, w, n, eps2, dev, stream):
                 fn()
                 g = sp2.sp2_graph_end(c.ctx)
                 gms = timed(lambda: sp2.sp2_graph_launch(c.ctx, g), reps, stream)
+                # the same graph replayed back to back (steps issued without a
+                # host wait in between, as a device-driven block loop runs them)
+                bms = timed(lambda: [sp2.sp2_graph_launch(c.ctx, g) for _ in range(20)], max(2, reps // 4), stream) / 20
                 sp2.sp2_graph_destroy(g)
                 row["mixed_graph_us_per_step"] = 1e3 * gms
+                row["mixed_graph_back_to_back_us_per_step"] = 1e3 * bms
                 if na <= 64:
                     # the fused pass reads each source's double-single cache
                     # once (112 B); the sweep does not flush L2 between steps
