@@ -2083,9 +2083,23 @@ __device__ __forceinline__ void device_shape(ForceParams &q) {
     q.sink_major = q.split >= kWarpReduceMinSplit ? 1 : 0;
 }
 
+// Resident CTAs of kMaxThreads that a kernel's register budget must allow
+// (0: no bound beyond the block size, the compiler's own choice).  The mixed
+// Hermite-4 force pass with nearest neighbour and two sinks per thread (the
+// large-N_active kernel) is held to 128 registers, which leaves 16 warps per
+// SM instead of 12 at its natural 164; ptxas then spills ~80 bytes, and the
+// pass runs 1 % faster (measured at N = N_active = 131072 with the autotuned
+// shape).  The same bound on the variant without neighbours (96 bytes of
+// spills) made the adjoint benchmark's forward passes 16 % slower, so that
+// one keeps its registers.
+template <class P, int IPT, bool FUSED>
+struct pass_min_blocks { static constexpr int value = 0; };
+template <>
+struct pass_min_blocks<MixedPairForce<4, true>, 2, false> { static constexpr int value = 2; };
+
 // MODE 0: the pass; 1: the device-count form; 2: several warps per sink.
 template <class P, int IPT, bool FUSED, int MODE = 0>
-__global__ void __launch_bounds__(kMaxThreads) pass_kernel(const ForceParams p) {
+__global__ void __launch_bounds__(kMaxThreads, (pass_min_blocks<P, IPT, FUSED>::value)) pass_kernel(const ForceParams p) {
     constexpr bool DEVN = MODE == 1;
     if constexpr (MODE == 2) {
         pass_body<P, IPT, FUSED, true>(p);
