@@ -518,6 +518,7 @@ def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.
             res["c1"] = bench_c1(sp2, dev, stream)
         if "sweep" in sections:
             res["sweep"] = sweep(sp2, w, n, eps2, dev, stream)
+            res["graph_launch_floor"] = graph_launch_floor(dev, stream)
         if "h6" in sections:
             res["h6"] = bench_h6(sp2, dev, stream)
         if "batched" in sections:
@@ -534,6 +535,23 @@ def extras(sp2, w, n, eps2, dev, stream, sections, blk_t_end=0.25, blk6_t_end=1.
             res["blk6"] = [r for nb in blk6_n for e in blk6_eps
                            for r in bench_blk6(sp2, dev, stream, n=nb, t_end=blk6_t_end, eps=e)]
     return res
+
+
+def graph_launch_floor(dev, stream):
+    """Context for the small-N_active steps: a CUDA graph of one trivial
+    kernel (a one-element add), timed as the sweep times its graphs -- once
+    per host wait, and replayed 20 times back to back."""
+    import torch
+    x = torch.zeros(1, device=dev)
+    x.add_(1)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        x.add_(1)
+    stream.synchronize()
+    one = timed(g.replay, 20, stream)
+    b2b = timed(lambda: [g.replay() for _ in range(20)], 5, stream) / 20
+    return {"kernel": "one-element add", "us_per_launch": 1e3 * one, "back_to_back_us_per_launch": 1e3 * b2b}
 
 
 def bench_c1(sp2, dev, stream):
