@@ -1514,64 +1514,67 @@ template <class P, class Write>
 __device__ __forceinline__ void reduce_sink_fields(const double *row, const int32_t *row_id, int split, double *s_f,
                                                    long long &s_nd, int &s_nid, const Write &write) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    // sums: warp w takes fields w, w + nw, ... two at a time with their adds
-    // interleaved (independent chains)
-    for (int f0 = warp; f0 < P::NS; f0 += 2 * nw) {
-        const bool two = f0 + nw < P::NS;  // (warp-uniform)
-        const double *col0 = row + static_cast<int64_t>(f0) * split;
-        const double *col1 = row + static_cast<int64_t>(two ? f0 + nw : f0) * split;
-        // lane l adds slices l, l + 32, l + 64, ... in that order; the loads of
-        // 256 slices per field are all issued before the first add
+    // columns 0 .. NS-1 are the summed fields and (with nearest neighbour)
+    // column NS the neighbour candidates; warp w takes columns w, w + nw, ...
+    // two at a time, so the neighbour's loads travel with a field's
+    constexpr int NC = P::NS + (P::kNN ? 1 : 0);
+    for (int c0 = warp; c0 < NC; c0 += 2 * nw) {
+        const int c1 = c0 + nw;
+        const bool two = c1 < NC;  // (warp-uniform)
+        const bool nn0 = P::kNN && c0 == P::NS, nn1 = P::kNN && two && c1 == P::NS;
+        const double *col0 = row + static_cast<int64_t>(c0) * split;
+        const double *col1 = row + static_cast<int64_t>(two ? c1 : c0) * split;
+        // lane l takes slices l, l + 32, l + 64, ... in that order; the loads of
+        // 256 slices per column are all issued before the first add
         double v0 = 0.0, v1 = 0.0;
+        long long d = 0x7ff0000000000000LL;  // neighbour column: best r^2 bits (+inf) and id
+        int id = -1;
         for (int s0 = 0; s0 < split; s0 += 8 * 32) {
             double x0[8], x1[8];
+            int xi[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int s = s0 + lane + 32 * e;
                 x0[e] = (s < split) ? __ldcg(col0 + s) : 0.0;
                 x1[e] = (two && s < split) ? __ldcg(col1 + s) : 0.0;
+                xi[e] = ((nn0 || nn1) && s < split) ? __ldcg(row_id + s) : -1;
             }
 #pragma unroll
             for (int e = 0; e < 8; ++e)
                 if (s0 + lane + 32 * e < split) {
-                    v0 += x0[e];
-                    if (two) v1 += x1[e];
+                    if (nn0 || nn1) {
+                        // non-negative r^2: the bit patterns order like the values
+                        const long long xd = __double_as_longlong(nn0 ? x0[e] : x1[e]);
+                        if (xd < d || (xd == d && static_cast<unsigned>(xi[e]) < static_cast<unsigned>(id))) {
+                            d = xd;
+                            id = xi[e];
+                        }
+                    }
+                    if (!nn0) v0 += x0[e];
+                    if (two && !nn1) v1 += x1[e];
                 }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            v0 += __shfl_xor_sync(kFull, v0, off);
-            if (two) v1 += __shfl_xor_sync(kFull, v1, off);
+            if (!nn0) v0 += __shfl_xor_sync(kFull, v0, off);
+            if (two && !nn1) v1 += __shfl_xor_sync(kFull, v1, off);
+            if (nn0 || nn1) {
+                const long long od = __shfl_xor_sync(kFull, d, off);
+                const int oid = __shfl_xor_sync(kFull, id, off);
+                if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) {
+                    d = od;
+                    id = oid;
+                }
+            }
         }
         if (lane == 0) {
-            s_f[f0] = v0;
-            if (two) s_f[f0 + nw] = v1;
-        }
-    }
-    if (P::kNN && warp == nw - 1) {
-        const double *col = row + static_cast<int64_t>(P::NS) * split;
-        long long d = 0x7ff0000000000000LL;  // +inf
-        int id = -1;
-        for (int s0 = 0; s0 < split; s0 += 8 * 32) {
-            long long xd[8];
-            int xi[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int s = s0 + lane + 32 * q;
-                xd[q] = (s < split) ? __double_as_longlong(__ldcg(col + s)) : 0x7ff0000000000000LL;
-                xi[q] = (s < split) ? __ldcg(row_id + s) : -1;
+            if (!nn0) s_f[c0] = v0;
+            if (two && !nn1) s_f[c1] = v1;
+            if (nn0 || nn1) {
+                s_nd = d;
+                s_nid = id;
             }
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (xd[q] < d || (xd[q] == d && static_cast<unsigned>(xi[q]) < static_cast<unsigned>(id))) { d = xd[q]; id = xi[q]; }
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const long long od = __shfl_xor_sync(kFull, d, off);
-            const int oid = __shfl_xor_sync(kFull, id, off);
-            if (od < d || (od == d && static_cast<unsigned>(oid) < static_cast<unsigned>(id))) { d = od; id = oid; }
-        }
-        if (lane == 0) { s_nd = d; s_nid = id; }
     }
     __syncthreads();
     if (tid == 0) {
