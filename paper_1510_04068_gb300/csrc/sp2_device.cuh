@@ -1586,6 +1586,43 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
     __syncthreads();
 }
 
+// One lane's share of a sink-major row: slices lane, lane + 32, ... of every
+// field added in that order (FP64) and the lexicographic (r^2, id) minimum of
+// their neighbours; the loads of a few slices (every field) are issued before
+// their adds, so a row of a few hundred slices costs one or two memory round
+// trips instead of one per slice.
+template <class P>
+__device__ __forceinline__ void lane_sum_slices(const double *row, const int32_t *row_id, int split, int lane,
+                                                double *t, double &nd, int &nid) {
+    constexpr int E = (P::NS <= 7) ? 4 : 2;  // slices in flight per lane
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    nd = d_inf();
+    nid = -1;
+    for (int s0 = 0; s0 < split; s0 += E * 32) {
+        double x[E][P::NS], xd[E];
+        int xi[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int s = s0 + lane + 32 * e;
+            const bool in = s < split;
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) x[e][f] = in ? __ldcg(row + f * split + s) : 0.0;
+            if (P::kNN) {
+                xd[e] = in ? __ldcg(row + P::NS * split + s) : d_inf();
+                xi[e] = in ? __ldcg(row_id + s) : -1;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (s0 + lane + 32 * e < split) {
+#pragma unroll
+                for (int f = 0; f < P::NS; ++f) t[f] += x[e][f];
+                if (P::kNN) nn_merge(nd, nid, xd[e], xi[e]);
+            }
+    }
+}
+
 // Fused split-j reduction of one i-block, run by the last CTA to finish one
 // of its slices.  Partials are read from L2 (__ldcg: written by other SMs in
 // this launch) in slice order, so the result does not depend on which CTA
@@ -1637,15 +1674,9 @@ __device__ __noinline__ void reduce_iblock(const ForceParams &p, int64_t iblk) {
         const double *row = p.part + (i - r0) * NF * split;
         const int32_t *row_id = p.part_id + (i - r0) * split;
         double t[P::NS];
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
-        double nd = d_inf();
-        int nid = -1;
-        for (int s = lane; s < split; s += 32) {
-#pragma unroll
-            for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(row + f * split + s);
-            if (P::kNN) nn_merge(nd, nid, __ldcg(row + P::NS * split + s), __ldcg(row_id + s));
-        }
+        double nd;
+        int nid;
+        lane_sum_slices<P>(row, row_id, split, lane, t, nd, nid);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
@@ -2150,15 +2181,9 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
     const double *row = r.part + i * NF * r.split;
     const int32_t *row_id = r.part_id + i * r.split;
     double t[P::NS];
-#pragma unroll
-    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
-    double nd = d_inf();
-    int nid = -1;
-    for (int s = lane; s < r.split; s += 32) {
-#pragma unroll
-        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
-        if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
-    }
+    double nd;
+    int nid;
+    lane_sum_slices<P>(row, row_id, r.split, lane, t, nd, nid);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
