@@ -1588,9 +1588,9 @@ __device__ __forceinline__ void reduce_sink_fields(const double *row, const int3
 
 // One lane's share of a sink-major row: slices lane, lane + 32, ... of every
 // field added in that order (FP64) and the lexicographic (r^2, id) minimum of
-// their neighbours; the loads of a few slices (every field) are issued before
-// their adds, so a row of a few hundred slices costs one or two memory round
-// trips instead of one per slice.
+// their neighbours; beyond two slices per lane the loads of a few slices
+// (every field) are issued before their adds, so a row of a few hundred
+// slices costs one or two memory round trips instead of one per slice.
 template <class P>
 __device__ __forceinline__ void lane_sum_slices(const double *row, const int32_t *row_id, int split, int lane,
                                                 double *t, double &nd, int &nid) {
@@ -1599,6 +1599,16 @@ __device__ __forceinline__ void lane_sum_slices(const double *row, const int32_t
     for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
     nd = d_inf();
     nid = -1;
+    if (split <= 64) {
+        // one or two slices per lane: the plain loop (the chunks would be
+        // mostly empty, their predicated loads and adds pure cost)
+        for (int s = lane; s < split; s += 32) {
+#pragma unroll
+            for (int f = 0; f < P::NS; ++f) t[f] += __ldcg(row + f * split + s);
+            if (P::kNN) nn_merge(nd, nid, __ldcg(row + P::NS * split + s), __ldcg(row_id + s));
+        }
+        return;
+    }
     for (int s0 = 0; s0 < split; s0 += E * 32) {
         double x[E][P::NS], xd[E];
         int xi[E];
@@ -2181,9 +2191,17 @@ __global__ void reduce_warp_kernel(const ReduceParams r) {
     const double *row = r.part + i * NF * r.split;
     const int32_t *row_id = r.part_id + i * r.split;
     double t[P::NS];
-    double nd;
-    int nid;
-    lane_sum_slices<P>(row, row_id, r.split, lane, t, nd, nid);
+#pragma unroll
+    for (int f = 0; f < P::NS; ++f) t[f] = 0.0;
+    double nd = d_inf();
+    int nid = -1;
+    // (many warps in flight hide the loads here; the chunked loads of
+    // lane_sum_slices would only cost registers and occupancy)
+    for (int s = lane; s < r.split; s += 32) {
+#pragma unroll
+        for (int f = 0; f < P::NS; ++f) t[f] += row[f * r.split + s];
+        if (P::kNN) nn_merge(nd, nid, row[P::NS * r.split + s], row_id[s]);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
